@@ -1,0 +1,483 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix:
+closed forms, invariants, textbook values and an independent Philox
+implementation.  CPU only."""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_4127_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+K_B = 1.380649e-16
+
+
+# ------------------------------------------------------------------ Philox
+_TRITON_SNIPPET = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+
+@triton.jit
+def k(out_ptr, c0_ptr, c1_ptr, c2_ptr, c3_ptr, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    r0, r1, r2, r3 = tl.philox(seed, tl.load(c0_ptr + i), tl.load(c1_ptr + i),
+                               tl.load(c2_ptr + i), tl.load(c3_ptr + i), 10)
+    tl.store(out_ptr + 4 * i + 0, r0); tl.store(out_ptr + 4 * i + 1, r1)
+    tl.store(out_ptr + 4 * i + 2, r2); tl.store(out_ptr + 4 * i + 3, r3)
+
+cases = json.loads(sys.argv[1])
+res = []
+for seed, ctrs in cases:
+    N = len(ctrs)
+    cols = [torch.tensor([c[w] for c in ctrs], dtype=torch.int64).to(torch.uint32) for w in range(4)]
+    out = torch.zeros(4 * N, dtype=torch.uint32)
+    k[(1,)](out, cols[0], cols[1], cols[2], cols[3], seed, N)
+    res.append([int(v) & 0xFFFFFFFF for v in out.to(torch.int64).tolist()])
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_triton_reference():
+    """Philox-4x32-10 against Triton's own implementation (run on the CPU
+    interpreter), key = (seed low word, seed high word)."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    cases = []
+    for seed in (0, 0x1101412701, 0xFFFFFFFFFFFFFFFF, 0x0123456789ABCDEF):
+        ctrs = [[int(v) for v in rng.integers(0, 2**32, 4)] for _ in range(4)]
+        ctrs[0] = [0, 0, 0, 0]
+        cases.append([seed, ctrs])
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.run([sys.executable, "-c", _TRITON_SNIPPET, json.dumps(cases)],
+                         capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + out.stderr[-300:])
+    ref = json.loads(out.stdout.strip().splitlines()[-1])
+    for (seed, ctrs), r in zip(cases, ref):
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for i, c in enumerate(ctrs):
+            got = oracle.philox4x32_10(c, key)
+            assert [int(v) for v in got] == r[4 * i:4 * i + 4], (seed, c)
+
+
+def test_directions_isotropic_and_unit():
+    """Marsaglia (1972): |d| = 1, <d> = 0, <d_i^2> = 1/3 and d_z uniform on
+    [-1, 1] (Archimedes) for an isotropic emission PDF (Sec. 2)."""
+    from scipy import stats
+    n = 20000
+    D = np.array([oracle.direction(0x1101412701, 3, 5, p)[0] for p in range(n)])
+    assert np.max(np.abs(np.linalg.norm(D, axis=1) - 1.0)) < 4e-16
+    assert np.all(np.abs(D.mean(axis=0)) < 4.0 / math.sqrt(3 * n))
+    m2 = (D * D).mean(axis=0)
+    assert np.all(np.abs(m2 - 1.0 / 3.0) < 0.01)
+    for a in range(3):
+        assert stats.kstest((D[:, a] + 1) / 2, "uniform").pvalue > 1e-3
+    # distinct counters give distinct directions; same counter repeats
+    d0, _ = oracle.direction(1, 0, 0, 0)
+    d1, _ = oracle.direction(1, 0, 0, 1)
+    d2, _ = oracle.direction(1, 1, 0, 0)
+    assert not np.allclose(d0, d1) and not np.allclose(d0, d2)
+    assert np.array_equal(d0, oracle.direction(1, 0, 0, 0)[0])
+
+
+# ------------------------------------------------------------------ exp
+def _ulp_diff(a, b):
+    ia = np.array([a], np.float64).view(np.int64)[0]
+    ib = np.array([b], np.float64).view(np.int64)[0]
+    return abs(int(ia) - int(ib))
+
+
+def test_exp_neg_within_two_ulp_of_libm():
+    rng = np.random.default_rng(1)
+    taus = np.concatenate([rng.uniform(0, 50, 20000), rng.uniform(0, 1e-3, 2000),
+                           np.arange(0, 50, 0.5 * math.log(2)), [1e-300, 5e-324, 1e-10]])
+    worst = 0
+    for t in taus:
+        worst = max(worst, _ulp_diff(oracle.exp_neg(t), math.exp(-t)))
+    assert worst <= 2
+    assert oracle.exp_neg(0.0) == 1.0
+    assert oracle.exp_neg(50.0000001) == 0.0 and oracle.exp_neg(1e300) == 0.0
+    # the cut at 50 cannot change a rounded transmitted count
+    assert (2**63) * math.exp(-50.0) < 0.5
+
+
+# ------------------------------------------------------------ cross sections
+def test_cross_sections_thresholds_and_power_law():
+    E = np.array([13.6, 27.2, 24.6, 54.4, 108.8, 13.0, 20.0, 50.0])
+    s = oracle.cross_sections(E)
+    assert s[0, 0] == pytest.approx(6.30e-18, rel=1e-15)
+    assert s[0, 1] == pytest.approx(6.30e-18 / 8, rel=1e-15)     # E^-3
+    assert s[1, 2] == pytest.approx(7.83e-18, rel=1e-12)          # He I at threshold
+    assert s[2, 3] == pytest.approx(1.58e-18, rel=1e-15)
+    assert s[2, 4] == pytest.approx(1.58e-18 / 8, rel=1e-15)
+    assert s[0, 5] == 0 and s[1, 6] == 0 and s[2, 7] == 0         # below threshold
+    Eh = np.geomspace(24.6, 200, 50)
+    sh = oracle.cross_sections(Eh)[1]
+    assert np.all(np.diff(sh) < 0) and np.all(sh > 0)
+
+
+# ------------------------------------------------------------------ DDA
+def _empty_grid(n=8, dl_cm=1.0):
+    g = oracle.OracleGrid(n, n, n, n * dl_cm, n_H0=0.0, x_HII0=0.0)
+    g.add_sources(np.array([[0.5, 0.5, 0.5]]), np.array([1.0]), np.array([13.6]), np.array([1.0]))
+    g.freeze()
+    return g
+
+
+def _chord_to_exit(p, d, n):
+    t = math.inf
+    for a in range(3):
+        if d[a] > 0:
+            t = min(t, (n - p[a]) / d[a])
+        elif d[a] < 0:
+            t = min(t, -p[a] / d[a])
+    return t
+
+
+def test_dda_segments_sum_to_chord_and_stay_in_cells():
+    n = 8
+    g = _empty_grid(n)
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        p = rng.uniform(0, n, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        cr, N, esc, ab, (cells, segs) = g.trace(p, d, [1000], log=200)
+        assert esc == 1000 and ab == 0 and cr == len(cells)
+        assert abs(segs.sum() - _chord_to_exit(p, d, n)) < 1e-12 * max(1, segs.sum())
+        t = 0.0
+        prev = None
+        for c, s in zip(cells, segs):
+            mid = p + d * (t + 0.5 * s)
+            ijk = (c % n, (c // n) % n, c // (n * n))
+            assert all(ijk[a] <= mid[a] <= ijk[a] + 1 for a in range(3))
+            if prev is not None:   # 6-connected walk (zero-length corner steps skipped)
+                assert 1 <= sum(abs(ijk[a] - prev[a]) for a in range(3)) <= 3
+            prev = ijk
+            t += s
+
+
+def test_dda_axis_aligned_unit_segments_and_corner_escape():
+    n = 6
+    g = _empty_grid(n)
+    cr, N, esc, ab, (cells, segs) = g.trace([0.0, 2.5, 3.5], [1.0, 0.0, 0.0], [7], log=20)
+    assert cr == n and np.all(segs == 1.0)
+    assert list(cells) == [0 + n * (2 + n * 3) + i for i in range(n)]
+    # a packet from the corner heading out of the box escapes with no crossing
+    cr, N, esc, ab, _ = g.trace([0.0, 0.0, 0.0], [-0.6, 0.0, 0.8], [5], log=5)
+    assert cr == 0 and esc == 5
+
+
+def test_median_chord_through_cell():
+    """The median path of random rays through a unit cell is ~0.56 cell
+    (Sec. 3.3, citing Ciardi et al. 2001): loose statistical check of the DDA."""
+    g = _empty_grid(16)
+    rng = np.random.default_rng(11)
+    segs = []
+    for _ in range(400):
+        p = rng.uniform(0, 16, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        segs.append(g.trace(p, d, [1], log=100)[4][1][1:-1])
+    med = np.median(np.concatenate(segs))
+    assert 0.45 < med < 0.7
+
+
+# ------------------------------------------------------------ attenuation
+def test_axis_ray_attenuation_matches_eq1_by_hand():
+    """Eq. 1 on a tiny grid: a +x ray through a uniform neutral row has unit
+    segments and N_k = rint(N_{k-1} exp(-tau)) in each cell."""
+    n = 4
+    dl = 3e20
+    nH = 1e-3
+    g = oracle.OracleGrid(n, n, n, n * dl, n_H0=nH, x_HII0=0.0, isothermal=1)
+    g.add_sources(np.array([[0.5, 0.5, 0.5]]), np.array([1.0]), np.array([13.6]), np.array([1.0]))
+    g.freeze()
+    N0 = 123456789012345
+    cr, N, esc, ab, (cells, segs) = g.trace([0.0, 1.5, 2.5], [1.0, 0.0, 0.0], [N0], log=10)
+    tau = nH * 6.30e-18 * dl
+    expect = N0
+    dep = g.read(oracle.F_DEP_HI).reshape(-1)
+    for k, c in enumerate(cells):
+        nxt = int(np.rint(expect * math.exp(-tau)))
+        assert abs(dep[c] - (expect - nxt)) <= 1
+        expect = nxt
+    assert abs(esc - N0 * math.exp(-4 * tau)) <= 4
+    assert ab + esc == N0
+    assert ab == int(dep.sum())
+
+
+def test_species_split_follows_optical_depth_share():
+    """Absorbed photons go to the species by their share of tau (Sec. 2)."""
+    n = 3
+    dl = 1e20
+    g = oracle.OracleGrid(n, n, n, n * dl, n_H0=1e-2, he_over_h=0.1, x_HII0=0.5,
+                          x_HeII0=0.3, x_HeIII0=0.1, isothermal=0)
+    E = np.array([60.0])
+    g.add_sources(np.array([[0.5, 0.5, 0.5]]), np.array([1.0]), E, np.array([1.0]))
+    g.freeze()
+    N0 = 10**15
+    g.trace([0.0, 0.5, 0.5], [1.0, 0.0, 0.0], [N0])
+    s = oracle.cross_sections(E)[:, 0]
+    k = np.array([1e-2 * 0.5 * s[0], 1e-3 * 0.6 * s[1], 1e-3 * 0.3 * s[2]])
+    dHI = g.read(oracle.F_DEP_HI).reshape(-1)
+    dHeI = g.read(oracle.F_DEP_HEI).reshape(-1)
+    dHeII = g.read(oracle.F_DEP_HEII).reshape(-1)
+    tot = dHI + dHeI + dHeII
+    c = 0
+    assert tot[c] > 0
+    assert abs(dHeI[c] - tot[c] * k[1] / k.sum()) <= 1
+    assert abs(dHeII[c] - tot[c] * k[2] / k.sum()) <= 1
+    # heating: excess energies (E - E_th) in units of 2^F eV, F = ceil(log2(60 - 13.6))
+    F = 6
+    heat = (dHI[c] * (60 - 13.6) + dHeI[c] * (60 - 24.6) + dHeII[c] * (60 - 54.4)) / 2**F
+    assert abs(g.read(oracle.F_DEP_E).reshape(-1)[c] - heat) <= 1
+
+
+# ------------------------------------------------------------ budget
+def _small_hhe(n=12, n_src=3, seed=5):
+    rng = np.random.default_rng(seed)
+    nH = inputs.lognormal_field(n, 1.0, 1e-3, seed)
+    E, f = inputs.blackbody_bins(1e5)
+    g = oracle.OracleGrid(n, n, n, 6.6 * inputs.KPC_CM * n / 128, n_H=nH, he_over_h=0.08,
+                          x_HII0=0.3, x_HeII0=0.2, x_HeIII0=0.05, T0=1e3, seed=seed)
+    pos = rng.uniform(0, n, (n_src, 3))
+    ndot = rng.uniform(1e47, 1e49, n_src)
+    g.add_sources(pos, ndot, E, f)
+    return g, pos, ndot, E, f
+
+
+def test_photon_budget_closes_exactly():
+    """emitted = absorbed + escaped to the photon quantum (Sec. 2 termination:
+    a packet ends empty or leaving the box)."""
+    g, pos, ndot, E, f = _small_hhe()
+    dt = 0.05 * inputs.MYR_S
+    for k in range(3):
+        g.step(dt, 3 * 700)
+        b = g.read(oracle.F_BUDGET)
+        assert b[0] == b[1] + b[2]
+        dep = (g.read(oracle.F_DEP_HI).sum() + g.read(oracle.F_DEP_HEI).sum()
+               + g.read(oracle.F_DEP_HEII).sum())
+        assert dep == b[1]
+        assert b[4] == 2100 and b[3] > 0
+        # per-step quantum: n_src max(ndot) dt / 2^E in (2^61, 2^62]
+        X = 3 * ndot.max() * dt / 2.0 ** b[5]
+        assert 2.0**61 < X <= 2.0**62
+        # every source's photons are emitted, in quanta
+        assert abs(b[0] - sum(round(nd * dt / 2.0 ** b[5]) for nd in ndot)) <= 3
+
+
+def test_packet_windows_add_up_exactly():
+    """Deposition is additive per packet: two disjoint packet-id windows sum
+    to the full run, bit for bit (the basis of sampled parity and of
+    sharding packets across devices)."""
+    P = 3 * 400
+    outs = []
+    for win in [(0, 400), (0, 150), (150, 400)]:
+        g, *_ = _small_hhe()
+        g.set_options(chemistry=0, pkt_begin=win[0], pkt_end=win[1])
+        g.step(0.05 * inputs.MYR_S, P)
+        outs.append([g.read(fid) for fid in (oracle.F_DEP_HI, oracle.F_DEP_HEI,
+                                             oracle.F_DEP_HEII, oracle.F_DEP_E)]
+                    + [g.read(oracle.F_BUDGET)])
+    for i in range(4):
+        assert np.array_equal(outs[0][i], outs[1][i] + outs[2][i])
+    for i in range(5):
+        assert outs[0][4][i] == outs[1][4][i] + outs[2][4][i]
+
+
+# ------------------------------------------------------------ chemistry
+def test_rates_match_textbook_values():
+    """Hydrogen recombination coefficients at 5000/10^4/2x10^4 K (Osterbrock
+    1989, Table 2.1), hydrogenic scaling of He III, KWH96 Compton constant."""
+    for T, aB, aA in [(5000, 4.54e-13, 6.82e-13), (1e4, 2.59e-13, 4.18e-13), (2e4, 1.43e-13, 2.51e-13)]:
+        assert oracle.rates(T, 1)[0] == pytest.approx(aB, rel=0.03)
+        assert oracle.rates(T, 0)[0] == pytest.approx(aA, rel=0.05)
+    for T in (1e4, 3e4, 1e5):
+        for cb in (0, 1):
+            r, rq = oracle.rates(T, cb), oracle.rates(T / 4, cb)
+            assert r[2] == pytest.approx(2 * rq[0], rel=2e-3)      # alpha(HeIII) = 2 alpha_H(T/4)
+            assert r[14] == pytest.approx(8 * rq[12], rel=2e-3)    # rec cooling Z^3 scaling
+        r = oracle.rates(T, 1)
+        assert r[9] == pytest.approx(13.6 * 1.602176634e-12 * r[4], rel=1e-12)
+    assert oracle.compton_coef(2.7) == pytest.approx(5.41e-36, rel=5e-3)
+    # the paper: t_s = 5e8 yr is about four recombination times (Sec. 4.1)
+    g0 = json.load(open(os.path.join(GOLDEN, "test0_setup.json")))
+    t_rec = 1 / (oracle.rates(g0["T_K"], 1)[0] * g0["n_H_cm3"])
+    assert g0["t_sim_yr"] * 3.15576e7 / t_rec == pytest.approx(g0["t_sim_over_t_rec_stated"], rel=0.05)
+
+
+def test_pure_recombination_closed_form():
+    """x(t) = x0 / (1 + alpha n_H x0 t) at fixed T, no sources, no collisions."""
+    nH, T = 1e-3, 1e4
+    a = oracle.rates(T, 1)[0]
+    for t in (1e14, 1e15, 5e15):
+        st, n = oracle.chem_cell(t, nH=nH, xHII=1.0, T=T, isothermal=1, eps=1e-3,
+                                 max_sub=10**6, cool_mask=oracle.C_RECOMB)
+        exact = 1.0 / (1.0 + a * nH * t)
+        assert st["xHII"] == pytest.approx(exact, rel=2e-3), (t, n)
+
+
+def test_photoionisation_equilibrium_quadratic_root():
+    """Gamma (1 - x) = alpha n_H x^2 at constant Gamma (pure H, fixed T)."""
+    nH, T = 1e-3, 1e4
+    a = oracle.rates(T, 1)[0]
+    for G in (1e-14, 1e-12, 1e-10):
+        st, _ = oracle.chem_cell(1e17, nH=nH, xHII=1e-3, T=T, G_HI=G, isothermal=1,
+                                 cool_mask=oracle.C_RECOMB)
+        x = (-G + math.sqrt(G * G + 4 * a * nH * G)) / (2 * a * nH)
+        assert st["xHII"] == pytest.approx(x, rel=1e-6)
+
+
+def test_collisional_ionisation_equilibrium():
+    """beta(T) (1 - x) = alpha(T) x at fixed T without radiation."""
+    for T in (2e4, 5e4, 1e5, 3e5):
+        r = oracle.rates(T, 0)
+        st, _ = oracle.chem_cell(1e18, nH=1.0, xHII=0.5, T=T, isothermal=1, caseB=0)
+        x = r[4] / (r[4] + r[0])
+        assert st["xHII"] == pytest.approx(x, rel=1e-6)
+
+
+def test_helium_chain_detailed_balance():
+    """He I <-> He II <-> He III equilibrium at fixed n_e: x2/x1 = I1/R2 and
+    x3/x2 = I2/R3 (the chain is a birth-death process)."""
+    nH, nHe, T = 1e-2, 1e-9, 2e4
+    GH, G1, G2 = 1e-6, 3e-12, 1e-13
+    st, _ = oracle.chem_cell(1e18, nH=nH, nHe=nHe, xHII=1.0, xHeII=0.0, T=T, G_HI=GH,
+                             G_HeI=G1, G_HeII=G2, isothermal=1)
+    r = oracle.rates(T, 1)
+    ne = nH * st["xHII"] + nHe * (st["xHeII"] + 2 * st["xHeIII"])
+    x1 = 1 - st["xHeII"] - st["xHeIII"]
+    assert st["xHeII"] / x1 == pytest.approx((G1 + r[5] * ne) / ((r[1] + r[3]) * ne), rel=1e-6)
+    assert st["xHeIII"] / st["xHeII"] == pytest.approx((G2 + r[6] * ne) / (r[2] * ne), rel=1e-6)
+
+
+def test_photoheating_energy_invariant():
+    """With cooling, recombination and collisions off, the thermal energy
+    1.5 k n_tot T gains exactly (mean excess energy) x (photo-ionisations),
+    the change in particle number included (Sec. 2)."""
+    nH, nHe = 1e-3, 8e-5
+    eps_erg = 5.0 * 1.602176634e-12
+    for (G0, G1, G2) in [(1e-14, 0, 0), (3e-14, 1e-14, 2e-15)]:
+        x0, y20, y30, T0 = 0.1, 0.05, 0.01, 200.0
+        st, n = oracle.chem_cell(3e13, nH=nH, nHe=nHe, xHII=x0, xHeII=y20, xHeIII=y30, T=T0,
+                                 G_HI=G0, G_HeI=G1, G_HeII=G2, heat_per_ion=eps_erg,
+                                 cool_mask=0)
+        ne0 = nH * x0 + nHe * (y20 + 2 * y30)
+        ne1 = nH * st["xHII"] + nHe * (st["xHeII"] + 2 * st["xHeIII"])
+        e0 = 1.5 * K_B * (nH + nHe + ne0) * T0
+        e1 = 1.5 * K_B * (nH + nHe + ne1) * st["T"]
+        assert ne1 > ne0
+        assert e1 - e0 == pytest.approx(eps_erg * (ne1 - ne0), rel=1e-9)
+
+
+def test_compton_relaxation_closed_form():
+    """Fully ionised H coupled only to the CMB: T - T_cmb decays as
+    exp(-C t / (3 k)) with C the Compton coefficient per electron."""
+    Tc = 2.725 * 10
+    C = oracle.compton_coef(Tc)
+    tau = 3 * K_B / C
+    st, _ = oracle.chem_cell(0.5 * tau, nH=1e-3, xHII=1.0, T=1e4, T_cmb=Tc, eps=1e-4,
+                             max_sub=10**6, cool_mask=oracle.C_COMPTON)
+    exact = Tc + (1e4 - Tc) * math.exp(-0.5)
+    assert st["T"] == pytest.approx(exact, rel=2e-4)
+
+
+def test_isothermal_keeps_temperature():
+    st, _ = oracle.chem_cell(1e15, nH=1e-3, xHII=0.1, T=1e4, G_HI=1e-12,
+                             heat_per_ion=1e-11, isothermal=1)
+    assert st["T"] == 1e4
+
+
+# ------------------------------------------------------------ Stroemgren
+def _front(g, n_oct=8):
+    x = g.read(oracle.F_XHII)
+    return (3 * n_oct * x.sum() / (4 * math.pi)) ** (1 / 3)
+
+
+def test_stromgren_radius_closed_form_value():
+    """r_S = (3 Ndot / (4 pi alpha_B n_H^2))^(1/3) for the Test-0 setup."""
+    a = oracle.rates(1e4, 1)[0]
+    rS = (3 * 5e48 / (4 * math.pi * a * 1e-6)) ** (1 / 3)
+    assert rS == pytest.approx(1.664e22, rel=2e-3)
+    assert 1 / (a * 1e-3) / inputs.MYR_S == pytest.approx(122.3, rel=2e-3)
+
+
+def test_front_follows_analytic_expansion():
+    """H II front radius from the ionised volume (Sec. 4.1) follows
+    r_I = r_S (1 - exp(-t/t_rec))^(1/3) with 0.1 Myr steps."""
+    w = inputs.stromgren_32()
+    g = oracle.OracleGrid.from_box(w.boxes[0])
+    dl = w.boxes[0].box_cm / 32
+    a = oracle.rates(1e4, 1)[0]
+    rS = (3 * 5e48 / (4 * math.pi * a * 1e-6)) ** (1 / 3) / dl
+    trec = 1 / (a * 1e-3)
+    dt = 0.1 * inputs.MYR_S
+    for k in range(1, 101):
+        g.step(dt, 20000)
+        if k >= 20 and k % 20 == 0:
+            rI = rS * (1 - math.exp(-k * dt / trec)) ** (1 / 3)
+            assert abs(_front(g) - rI) < 0.05 * rI, k
+
+
+def test_front_lag_shrinks_with_time_step():
+    """The frozen-opacity step lags the analytic front; the lag shrinks as the
+    time step shrinks (10 Myr reached with 0.5 and with 0.1 Myr steps)."""
+    lags = []
+    w = inputs.stromgren_32()
+    dl = w.boxes[0].box_cm / 32
+    a = oracle.rates(1e4, 1)[0]
+    rS = (3 * 5e48 / (4 * math.pi * a * 1e-6)) ** (1 / 3) / dl
+    rI = rS * (1 - math.exp(-10 * inputs.MYR_S * a * 1e-3)) ** (1 / 3)
+    for nsteps, P in ((20, 50000), (100, 10000)):
+        g = oracle.OracleGrid.from_box(w.boxes[0])
+        for _ in range(nsteps):
+            g.step(10 * inputs.MYR_S / nsteps, P)
+        lags.append(rI - _front(g))
+    assert lags[0] > lags[1] > -0.5
+    assert lags[0] < 0.2 * rI
+
+
+def test_stromgren_equilibrium_after_four_recombination_times():
+    w = inputs.stromgren_32()
+    g = oracle.OracleGrid.from_box(w.boxes[0])
+    dl = w.boxes[0].box_cm / 32
+    a = oracle.rates(1e4, 1)[0]
+    rS = (3 * 5e48 / (4 * math.pi * a * 1e-6)) ** (1 / 3) / dl
+    for _ in range(100):
+        g.step(5 * inputs.MYR_S, 20000)
+    assert _front(g) == pytest.approx(rS, rel=0.05)
+
+
+def test_step_converts_deposits_to_ionisations_and_heat():
+    """Over a short step (x changes little) with recombination, collisions and
+    cooling off, the grid gains one electron per absorbed photon and the
+    thermal energy the deposited excess energy: pins the photon quantum, the
+    cell volume and the heat unit used by the per-cell update."""
+    g, pos, ndot, E, f = _small_hhe(n=10, n_src=2, seed=9)
+    g.set_options(cool_mask=0)
+    n = 10
+    V = (6.6 * inputs.KPC_CM * n / 128 / n) ** 3
+    nH = g.read(oracle.F_NH)
+    nHe = 0.08 * nH
+
+    def energy_and_ne():
+        x, y2, y3, T = (g.read(i) for i in (oracle.F_XHII, oracle.F_XHEII, oracle.F_XHEIII, oracle.F_T))
+        ne = nH * x + nHe * (y2 + 2 * y3)
+        return (1.5 * K_B * (nH + nHe + ne) * T * V).sum(), (ne * V).sum()
+
+    e0, n0 = energy_and_ne()
+    dt = 1e-6 * inputs.MYR_S
+    g.step(dt, 2 * 3000)
+    e1, n1 = energy_and_ne()
+    b = g.read(oracle.F_BUDGET)
+    q = 2.0 ** b[5]
+    heat = g.read(oracle.F_DEP_E).sum() * 2.0 ** (b[5] + b[6]) * 1.602176634e-12
+    assert n1 - n0 == pytest.approx(b[1] * q, rel=0.005)
+    assert e1 - e0 == pytest.approx(heat, rel=0.005)
