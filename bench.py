@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the radiative-transfer step: cell crossings per second.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl crash|reference]
+                [--workload NAME]
+
+One step = one whole pass of the hot path (source budget, emission, traversal
+with attenuation and int64 deposition, per-cell chemistry) over the
+workload's packets for one time step.  The metric is cell crossings per
+second: (packet, cell) segments with positive length, counted on the device.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), timed with CUDA events on the library's stream;
+every step moves a state far larger than L2 (or L2 is flushed between
+steps, see config.l2).  With N > 1 (torchrun) every rank runs an
+independent replica with its own seed (weak scaling; the step needs no
+exchange between replicas) and rank 0 prints the max-over-ranks time.
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload on the host cores (the baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell crossings/s"
+
+
+# ---------------------------------------------------------------- workloads
+def workload(name):
+    from paper_1101_4127_gb300 import inputs, native
+    if name == "hhe_bb_128":
+        w = inputs.hhe_blackbody_128()
+        return w, native.CRASH_FP64_PLAIN
+    if name == "stromgren_32":
+        return inputs.stromgren_32(), native.CRASH_FP64_PLAIN
+    if name == "lognormal_128":
+        return inputs.lognormal_128(), native.CRASH_MIXED
+    if name == "lognormal_512_thin":
+        return inputs.lognormal_512(thin=True), native.CRASH_MIXED
+    if name == "lognormal_512_neutral":
+        return inputs.lognormal_512(thin=False), native.CRASH_MIXED
+    raise SystemExit(f"unknown workload {name}")
+
+
+def bytes_per_crossing(box, precision):
+    """Algorithmic bytes one crossing must move: the crossed cell's frozen
+    absorbers (1 value for pure H, 3 with He; 8 B in FP64, 4 B in FP32) and its
+    deposit payload (one int64 per species present, plus the heating counter
+    when T evolves)."""
+    from paper_1101_4127_gb300 import native
+    he = box.he_over_h > 0
+    n_abs = 3 if he else 1
+    w = 8 if precision == native.CRASH_FP64_PLAIN else 4
+    n_dep = (3 if he else 1) + (0 if box.isothermal else 1)
+    return n_abs * w + 8 * n_dep
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(workload_name, kernel_src):
+    """DRAM bytes per crossing of the dominant kernel from the committed ncu
+    summary (profiles/traffic.md), if taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(p):
+        return None, None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:12]
+    for ln in open(p):
+        c = [x.strip() for x in ln.strip().strip("|").split("|")]
+        if len(c) >= 4 and c[0] == workload_name:
+            if c[1] == sha:
+                return float(c[2]), float(c[3])   # dram bytes per launch, crossings per launch
+            return None, None
+    return None, None
+
+
+# ---------------------------------------------------------------- reference arm
+def oracle_sample(w, seconds=15.0):
+    """Time the CPU oracle (one core) on a bounded sample of one step of the
+    workload and extrapolate to the whole step: the transport of packet ids
+    [0, K) of every source (K grown until it takes about seconds/2), plus the
+    per-cell chemistry of the step timed on the grid itself when it has at
+    most 128^3 cells, else on a 128^3 corner of it.  Returns
+    (crossings/s, description, seconds spent)."""
+    import oracle
+    from paper_1101_4127_gb300 import inputs
+    box = w.boxes[0]
+    P = w.packets_per_step[0]
+    Ns = P // box.n_src
+    K = 1
+    spent = 0.0
+    while True:
+        o = oracle.OracleGrid.from_box(box)
+        o.set_options(chemistry=0, pkt_begin=0, pkt_end=K)
+        t0 = time.perf_counter()
+        o.step(w.dt_s, P)
+        t_tr = time.perf_counter() - t0
+        spent += t_tr
+        cross = int(o.read(oracle.F_BUDGET)[3])
+        o.close()
+        if t_tr > seconds / 2 or K >= Ns:
+            break
+        K = min(Ns, max(K * 2, int(K * (seconds / 2) / max(t_tr, 1e-3))))
+    # chemistry of one step on (a corner of) the grid, with that step's deposits
+    m = min(box.n, 128)
+    sub = box
+    if m < box.n:
+        import copy
+        sub = copy.copy(box)
+        sub.n = m
+        sub.nH = np.ascontiguousarray(box.nH[:m, :m, :m]) if box.nH is not None else None
+        keep = np.all(box.src_pos < m, axis=1)
+        if not keep.any():
+            keep[:] = False
+            keep[0] = True
+            sub.src_pos = np.full((1, 3), 0.5 * m)
+        else:
+            sub.src_pos = box.src_pos[keep]
+        sub.src_ndot = box.src_ndot[keep][: len(sub.src_pos)]
+        sub.bin_frac = box.bin_frac[keep][: len(sub.src_pos)]
+    o = oracle.OracleGrid.from_box(sub)
+    Psub = sub.src_ndot.shape[0] * max(1, min(Ns, 64))
+    o.set_options(chemistry=0)
+    o.step(w.dt_s, Psub)
+    o.set_options(chemistry=1, pkt_begin=0, pkt_end=0)
+    t0 = time.perf_counter()
+    o.step(w.dt_s, Psub)               # chemistry only (empty packet window)
+    t_chem = time.perf_counter() - t0
+    spent += t_chem
+    o.close()
+    ncell = box.n ** 3
+    t_step = t_tr * (Ns / K) + t_chem * (ncell / m ** 3)
+    cross_step = cross * (Ns / K)
+    rate = cross_step / t_step
+    desc = (f"one step of {w.name}: transport of packet ids [0,{K}) of each of the {box.n_src} "
+            f"sources ({cross} crossings, {t_tr:.2f} s) scaled to {Ns} per source, plus chemistry "
+            f"timed on {m}^3 cells ({t_chem:.2f} s) scaled to {box.n}^3")
+    return rate, desc, spent
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, _prec = workload(args.workload)
+    vals = []
+    desc = ""
+    for _ in range(args.warmup):
+        oracle_sample(w, seconds=min(args.ref_seconds, 2.0))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, desc, el = oracle_sample(w, seconds=args.ref_seconds / max(1, args.steps))
+        vals.append(r)
+    total = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "crossings/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "crossings/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "crossings/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- main arm
+def run_crash(args):
+    import torch
+    from paper_1101_4127_gb300 import build, native
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        if rank == 0:
+            build.build()
+        dist.barrier()
+    else:
+        torch.cuda.set_device(0)
+        build.build()
+    dev = torch.device("cuda", local)
+
+    w, prec = workload(args.workload)
+    box = w.boxes[0]
+    box.seed = box.seed + rank          # independent replica per rank
+    P = w.packets_per_step[0]
+    g = native.Grid(box, prec)
+    g.set_options(timing=1)
+    stream = torch.cuda.ExternalStream(g.stream(), device=dev)
+    state_bytes = box.n ** 3 * (4 + 4 * 8 + 32 + (32 if prec == native.CRASH_FP64_PLAIN else 16))
+    l2_bytes = 129 * 2**20
+    flush = None
+    if state_bytes < 2 * l2_bytes:
+        flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+        g.step(w.dt_s, P)
+
+    for _ in range(args.warmup):
+        one_step()
+    g.sync()
+    g.reset_kernel_time()
+    tot0 = g.read(native.F_TOTALS)
+    launches0 = g.launch_count()
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    tot1 = g.read(native.F_TOTALS)
+    launches = g.launch_count() - launches0
+    kms, klaunches = g.kernel_time()
+    crossings = int(tot1[3] - tot0[3])
+    if dist:
+        t = torch.tensor([ms, float(crossings)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_max = float(tmax[0])
+        cross_all = float(tsum[1])
+    else:
+        ms_max, cross_all = ms, float(crossings)
+    value = cross_all / (ms_max * 1e-3)
+
+    # roofline of the dominant (transport) kernel
+    bx = bytes_per_crossing(box, prec)
+    peak, peak_kind = measured_peaks()
+    achieved = (crossings * bx) / (kms * 1e-3) / 1e9 if kms > 0 else None
+    ksrc = os.path.join(ROOT, "paper_1101_4127_gb300", "csrc",
+                        "k_fp64.cu" if prec == native.CRASH_FP64_PLAIN else "k_mixed.cu")
+    dram_per_launch, cross_per_launch = traffic_for(args.workload, ksrc)
+    traffic = None
+    if dram_per_launch is not None and klaunches:
+        # scale the captured launch to this run's average launch by crossings
+        traffic = dram_per_launch * (crossings / klaunches) / cross_per_launch
+
+    # end-to-end through the C ABI with host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        g.set_options(timing=0)
+        xh = np.empty(box.n ** 3, np.float64)
+        bud = np.empty(8, np.int64)
+        nb = len(box.bin_eV)
+        h2d = box.n_src * (3 + 1 + nb) * 8 + nb * 8
+        d2h = xh.nbytes + bud.nbytes
+        t_e2e = 0.0
+        cr_e2e = 0
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            t0 = time.perf_counter()
+            g.add_sources(box.src_pos, box.src_ndot, box.bin_eV, box.bin_frac)
+            g.step(w.dt_s, P)
+            g._check(g.L.crash_read_fields(g.ctx, native.F_XHII, xh.ctypes.data))
+            g._check(g.L.crash_read_fields(g.ctx, native.F_BUDGET, bud.ctypes.data))
+            t_e2e += time.perf_counter() - t0
+            cr_e2e += int(bud[3])
+        e2e = {"value": cr_e2e / t_e2e, "unit": "crossings/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, desc, _ = oracle_sample(w, seconds=args.ref_seconds)
+        cpu = {"value": r, "unit": "crossings/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "crossings/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == native.CRASH_FP64_PLAIN else "f32+i64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": box.n, "sources": box.n_src,
+                       "packets_per_step": P, "bins": len(box.bin_eV),
+                       "precision": "fp64" if prec == native.CRASH_FP64_PLAIN else "mixed",
+                       "l2": "flushed between steps (256 MiB write)" if flush is not None
+                             else "state larger than L2",
+                       "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "transport", "bytes_per_crossing": bx,
+                         "kernel_ms_per_launch": kms / max(1, klaunches)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": ck,
+            "crossings_per_step": crossings / args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="crash", choices=["crash", "reference"])
+    ap.add_argument("--workload", default="hhe_bb_128")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_crash(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * crash.h -- C ABI of the GB300 (sm_103a) Monte-Carlo radiative-transfer step.
+ *
+ * The library runs the data-parallel hot path of a CRASH2-style step
+ * (arXiv:1101.4127, Sec. 2 and Sec. 3.2) on one GPU:
+ *   emission of photon packets from point sources (Sec. 2: coloured packets,
+ *   N_p/N_t packets per source per step, Sec. 3.2), cell-by-cell propagation
+ *   through a 3D Cartesian grid with attenuation by the H I / He I / He II
+ *   optical depth (Sec. 2, Eq. 1) and deposition of the absorbed photons in
+ *   the crossed cells, followed by the per-cell ionisation network and
+ *   temperature update (Sec. 2; sub-sampled as in Sec. 3.2).
+ *
+ * Conventions shared by every call:
+ *   - Grids are nx*ny*nz cubic cells stored x fastest: cell (i,j,k) has the
+ *     linear index i + nx*(j + ny*k).  Positions are in grid units: cell
+ *     (i,j,k) spans [i,i+1) x [j,j+1) x [k,k+1).
+ *   - Units are cgs: cm, s, cm^-3, K, photons/s, eV for photon energies.
+ *   - Every pointer argument is a HOST pointer unless the name ends in _dev.
+ *     The caller owns its buffers; the library copies what it needs before
+ *     the call returns.  The context owns all device memory and one CUDA
+ *     stream; nothing is shared between contexts.
+ *   - Functions never abort.  They return a crash_status and, on failure,
+ *     leave a message for crash_last_error().  A CRASH_ERR_CUDA or
+ *     CRASH_ERR_TIMEOUT result leaves the context usable only for
+ *     crash_read_fields and crash_free.
+ *   - The transported photons are integers in units of a per-step quantum
+ *     q = 2^E (E chosen per box and step so that n_src * max(ndot) * dt / q
+ *     <= 2^62), so emitted = absorbed + escaped holds exactly.
+ */
+#ifndef CRASH_H
+#define CRASH_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crash_ctx crash_ctx;   /* opaque; owns all device memory */
+
+typedef enum {
+  CRASH_OK = 0,
+  CRASH_ERR_ARG = -1,        /* invalid argument (message says which) */
+  CRASH_ERR_OOM = -2,        /* device or host allocation failed */
+  CRASH_ERR_CUDA = -3,       /* a CUDA call or kernel failed */
+  CRASH_ERR_OVERFLOW = -4,   /* a capacity (packets, bins, queue) would be exceeded */
+  CRASH_ERR_TIMEOUT = -5,    /* a device-side bounded loop hit its limit */
+  CRASH_ERR_STATE = -6       /* call out of order (e.g. crash_step before sources) */
+} crash_status;
+
+typedef enum {
+  CRASH_FP64_PLAIN = 0,      /* FP64 transport, bit-exact with the FP64 specification */
+  CRASH_MIXED = 1            /* FP32 traversal/attenuation, int64 deposits, FP64 chemistry */
+} crash_precision;
+
+/* Field ids for crash_read_fields / crash_write_fields. */
+typedef enum {
+  CRASH_F_XHII = 0, CRASH_F_XHEII = 1, CRASH_F_XHEIII = 2, CRASH_F_T = 3, /* double per cell (r/w) */
+  CRASH_F_DEP_HI = 4, CRASH_F_DEP_HEI = 5, CRASH_F_DEP_HEII = 6,          /* int64 per cell, last step */
+  CRASH_F_DEP_E = 7,        /* int64 per cell: excess energy in units of q * 2^F eV */
+  CRASH_F_BUDGET = 8,       /* int64[8]: emitted, absorbed, escaped, crossings,
+                               packets traced, quantum exponent E, heat exponent F,
+                               chemistry sub-steps (all for the last step) */
+  CRASH_F_NH = 9,           /* double per cell: n_H (read only) */
+  CRASH_F_TOTALS = 10       /* int64[8]: slots 0-4 and 7 of CRASH_F_BUDGET summed over all
+                               steps since the context was created (slots 5, 6: last step) */
+} crash_field;
+
+/* One grid and its initial state.  Section 2 of the paper: a static H/He
+   density field on a Cartesian grid whose ionisation fractions and
+   temperature evolve. */
+typedef struct {
+  int nx, ny, nz;            /* cells per axis, each >= 1 */
+  double box_cm;             /* length of the x edge; cell edge dl = box_cm / nx */
+  const float* n_H;          /* nx*ny*nz hydrogen densities (cm^-3); NULL => n_H0 everywhere */
+  double n_H0;
+  double he_over_h;          /* helium-to-hydrogen number ratio; 0 => pure hydrogen */
+  const double *x_HII, *x_HeII, *x_HeIII, *T;   /* initial state per cell; NULL => uniform value */
+  double x_HII0, x_HeII0, x_HeIII0, T0;
+  int isothermal;            /* 1: T stays fixed (no heating deposit, no T update) */
+  int caseB;                 /* 1: case-B recombination (on-the-spot), 0: case A */
+  double z_compton;          /* redshift of the CMB for Compton exchange; < 0 => off */
+  uint64_t seed;             /* Philox key of this grid */
+  int precision;             /* crash_precision; must be equal for all boxes of a batch */
+} crash_grid_desc;
+
+/* Run options (crash_default_opts fills the defaults). */
+typedef struct {
+  int chemistry;             /* 1: per-cell update after transport (default); 0: transport only */
+  uint32_t pkt_begin, pkt_end; /* trace only packet ids p in [pkt_begin, pkt_end) of each source
+                                  (default 0, 0xFFFFFFFF: all); contents are those of the full step */
+  double chem_eps;           /* allowed relative change per chemistry sub-step (default 0.1) */
+  int chem_max_sub;          /* sub-step cap per cell and step (default 10000) */
+  int cool_mask;             /* processes on: 1 coll. excitation, 2 coll. ionisation, 4 recombination,
+                                8 bremsstrahlung, 16 Compton, 32 dielectronic (default 63) */
+  int block_size;            /* threads per block of the transport kernels (0 = tuned/default) */
+  int seg_per_iter;          /* mixed form: crossings per packet per wavefront pass (0 = tuned) */
+  int resort_interval;       /* mixed form: wavefront passes between Morton re-sorts (0 = tuned,
+                                <0 = never) */
+  int wavefront;             /* mixed form: 1 = packet-queue wavefront, 0 = one thread per packet */
+  int use_graph;             /* 1: capture each step in a CUDA graph and replay it */
+  int timing;                /* 1: record CUDA events around the transport launches */
+} crash_run_opts;
+
+void crash_default_opts(crash_run_opts* o);
+
+/* Create a context holding one grid (equivalent to a batch of one). */
+crash_status crash_init_grid(const crash_grid_desc* desc, crash_ctx** out);
+
+/* Create a context holding n_boxes independent grids that step together
+   (the batched form).  Each box keeps its own seed, sources and budget. */
+crash_status crash_init_batch(int n_boxes, const crash_grid_desc* descs, crash_ctx** out);
+
+/* Sources of box `box` (Sec. 2: point sources with luminosity and spectrum).
+   pos_cells: n_src*3 grid-unit positions inside [0,nx)x[0,ny)x[0,nz);
+   ndot: n_src photon rates (photons/s, >= 0);
+   bin_eV: n_bins bin energies (eV, > 0), 1 <= n_bins <= 16, identical for all boxes;
+   bin_frac: n_src*n_bins photon-number fractions per source (>= 0; the last bin
+   takes what the cumulative fractions leave).  Replaces earlier sources. */
+crash_status crash_add_sources(crash_ctx* ctx, int n_src, const double* pos_cells,
+                               const double* ndot, int n_bins, const double* bin_eV,
+                               const double* bin_frac);
+crash_status crash_add_sources_box(crash_ctx* ctx, int box, int n_src, const double* pos_cells,
+                                   const double* ndot, int n_bins, const double* bin_eV,
+                                   const double* bin_frac);
+
+crash_status crash_set_options(crash_ctx* ctx, const crash_run_opts* opts);
+
+/* One time step of length dt_s (Sec. 2 and Sec. 3.2): every box emits
+   packets_per_step packets split equally over its sources (must be a
+   multiple of each box's source count), traces them against the absorbers
+   frozen at the start of the step, then (if enabled) updates every cell.
+   The call is asynchronous on the context stream except for argument checks;
+   read_fields and sync wait for it. */
+crash_status crash_step(crash_ctx* ctx, double dt_s, uint64_t packets_per_step);
+/* Batched form: per-box packet counts (n_boxes entries). */
+crash_status crash_step_batch(crash_ctx* ctx, double dt_s, const uint64_t* packets_per_box);
+
+/* Copy a field of box 0 / of box `box` to host memory (size: cells of the box
+   times 8 bytes, or 64 bytes for CRASH_F_BUDGET).  Synchronises the stream. */
+crash_status crash_read_fields(crash_ctx* ctx, int field_id, void* host_out);
+crash_status crash_read_fields_box(crash_ctx* ctx, int box, int field_id, void* host_out);
+/* Overwrite a state field (x_HII, x_HeII, x_HeIII or T) of box 0 / `box` from host memory. */
+crash_status crash_write_fields(crash_ctx* ctx, int field_id, const void* host_in);
+crash_status crash_write_fields_box(crash_ctx* ctx, int box, int field_id, const void* host_in);
+
+/* Step counter used as the Philox counter word (resume: restore the fields,
+   then set the index of the next step). */
+crash_status crash_set_step_index(crash_ctx* ctx, uint64_t step);
+crash_status crash_sync(crash_ctx* ctx);
+
+/* Event-timed transport: total milliseconds and launch count of the dominant
+   transport kernel since the last reset (needs opts.timing = 1). */
+crash_status crash_kernel_time(crash_ctx* ctx, double* ms_total, int64_t* launches);
+crash_status crash_reset_kernel_time(crash_ctx* ctx);
+
+/* The context's CUDA stream (a cudaStream_t) for callers that time or order
+   work around crash_step. */
+void* crash_stream(crash_ctx* ctx);
+
+/* Number of kernel launches the context has enqueued since it was created
+   (graph replays count the kernels inside the graph). */
+int64_t crash_launch_count(crash_ctx* ctx);
+
+/* Autotuner: times trial steps over block size, crossings per pass and
+   re-sort interval on the current state (which is saved and restored) and
+   stores the fastest in the context's options; returns the chosen values. */
+crash_status crash_autotune(crash_ctx* ctx, double dt_s, const uint64_t* packets_per_box,
+                            int* block_size, int* seg_per_iter, int* resort_interval);
+
+crash_status crash_free(crash_ctx* ctx);
+const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -194,7 +194,8 @@ class OracleGrid:
 
     @classmethod
     def from_box(cls, box, precision_unused=None):
-        g = cls(box.n, box.n, box.n, box.box_cm, n_H=box.nH, n_H0=box.nH0,
+        nx, ny, nz = box.shape_xyz
+        g = cls(nx, ny, nz, box.box_cm, n_H=box.nH, n_H0=box.nH0,
                 he_over_h=box.he_over_h, x_HII0=box.x_HII0, x_HeII0=box.x_HeII0,
                 x_HeIII0=box.x_HeIII0, T0=box.T0, isothermal=box.isothermal,
                 caseB=box.caseB, z_compton=box.z_compton, seed=box.seed)

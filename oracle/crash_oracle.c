@@ -206,7 +206,8 @@ or_ctx* oracle_init_grid(const or_grid_desc* d) {
     return NULL;
   }
   for (size_t i = 0; i < n; ++i) {
-    c->nH[i] = d->n_H ? (double)d->n_H[i] : d->n_H0;
+    /* densities are single-precision inputs; a uniform value is rounded the same way */
+    c->nH[i] = d->n_H ? (double)d->n_H[i] : (double)(float)d->n_H0;
     c->xHII[i] = d->x_HII ? d->x_HII[i] : d->x_HII0;
     c->xHeII[i] = d->x_HeII ? d->x_HeII[i] : d->x_HeII0;
     c->xHeIII[i] = d->x_HeIII ? d->x_HeIII[i] : d->x_HeIII0;

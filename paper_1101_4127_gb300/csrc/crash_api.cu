@@ -1,0 +1,749 @@
+// crash_api.cu -- host runtime behind the C ABI of include/crash.h: context
+// and device memory, source tables, the per-step launch sequence (optionally
+// captured in a CUDA graph), field I/O, event timing and the autotuner.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "crash_internal.cuh"
+
+namespace {
+
+// ionisation thresholds of H I, He I, He II (eV)
+constexpr double kEth[3] = {13.6, 24.6, 54.4};
+thread_local std::string g_create_error;
+
+struct BoxHost {
+  crash_grid_desc d;
+  std::vector<double> pos, ndot, frac;   // sources of this box
+  bool has_sources = false;
+};
+
+}  // namespace
+
+struct crash_ctx {
+  int n_boxes = 0;
+  int precision = CRASH_FP64_PLAIN;
+  std::vector<BoxHost> bh;
+  std::vector<BoxMeta> meta;
+  int64_t n_cells = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // device buffers
+  float* nH = nullptr;
+  double *xHII = nullptr, *xHeII = nullptr, *xHeIII = nullptr, *T = nullptr;
+  double* abs64 = nullptr;
+  float* abs32 = nullptr;
+  unsigned long long* dep = nullptr;
+  BoxMeta* d_meta = nullptr;
+  unsigned long long* budget = nullptr;
+  unsigned long long* totals = nullptr;   // [n_boxes][8] running sums of the budget
+  unsigned long long* step_dev = nullptr;
+  int* err = nullptr;
+  int* boxE = nullptr;
+  double *src_pos = nullptr, *src_ndot = nullptr, *src_frac = nullptr;
+  int64_t *src_base = nullptr, *src_rem = nullptr;
+  int n_src_total = 0, src_cap = 0;
+  // bins
+  int n_bins = 0;
+  std::vector<double> bin_eV;
+  BinTables tables{};
+  // options / state
+  crash_run_opts opts{};
+  uint64_t step_host = 0;
+  bool any_he = false, any_heat = false;
+  std::string error;
+  // timing
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  int ev_used = 0;
+  double ms_accum = 0.0;
+  int64_t launches_accum = 0;
+  // graph of one step
+  cudaGraphExec_t graph = nullptr;
+  std::vector<uint64_t> graph_key;
+  // mixed-form wavefront workspace
+  void* wf = nullptr;
+  int64_t launches = 0;          // kernels enqueued so far
+  int64_t graph_launches = 0;    // kernels inside the captured step graph
+};
+
+static crash_status set_err(crash_ctx* c, crash_status st, const std::string& msg) {
+  if (c) c->error = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return set_err(c, e_ == cudaErrorMemoryAllocation ? CRASH_ERR_OOM : CRASH_ERR_CUDA, \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+extern "C" void crash_default_opts(crash_run_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->chemistry = 1;
+  o->pkt_begin = 0;
+  o->pkt_end = 0xFFFFFFFFu;
+  o->chem_eps = 0.1;
+  o->chem_max_sub = 10000;
+  o->cool_mask = 63;
+  o->block_size = 0;
+  o->seg_per_iter = 0;
+  o->resort_interval = 0;
+  o->wavefront = 1;
+  o->use_graph = 0;
+  o->timing = 0;
+}
+
+// ---------------------------------------------------------------- teardown
+static void release(crash_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto& e : c->events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (c->wf) wavefront_destroy(c->wf);
+  void* ptrs[] = {c->nH, c->xHII, c->xHeII, c->xHeIII, c->T, c->abs64, c->abs32, c->dep,
+                  c->d_meta, c->budget, c->totals, c->step_dev, c->err, c->boxE, c->src_pos, c->src_ndot,
+                  c->src_frac, c->src_base, c->src_rem};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" crash_status crash_free(crash_ctx* c) {
+  if (!c) return CRASH_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  release(c);
+  return CRASH_OK;
+}
+
+extern "C" const char* crash_last_error(crash_ctx* c) {
+  return c ? c->error.c_str() : g_create_error.c_str();
+}
+
+extern "C" void* crash_stream(crash_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+extern "C" int64_t crash_launch_count(crash_ctx* c) { return c ? c->launches : -1; }
+
+// ---------------------------------------------------------------- creation
+static crash_status validate_desc(const crash_grid_desc& d, int i) {
+  crash_ctx* c = nullptr;
+  char buf[160];
+  if (d.nx < 1 || d.ny < 1 || d.nz < 1) {
+    snprintf(buf, sizeof buf, "box %d: nx, ny, nz must be >= 1", i);
+    return set_err(c, CRASH_ERR_ARG, buf);
+  }
+  if (!(d.box_cm > 0)) return set_err(c, CRASH_ERR_ARG, "box_cm must be positive");
+  if (!(d.he_over_h >= 0)) return set_err(c, CRASH_ERR_ARG, "he_over_h must be >= 0");
+  if (d.precision != CRASH_FP64_PLAIN && d.precision != CRASH_MIXED)
+    return set_err(c, CRASH_ERR_ARG, "unknown precision");
+  if ((int64_t)d.nx * d.ny * d.nz > ((int64_t)1 << 40))
+    return set_err(c, CRASH_ERR_OVERFLOW, "grid too large");
+  if (!d.T && !(d.T0 > 0)) return set_err(c, CRASH_ERR_ARG, "T0 must be positive");
+  return CRASH_OK;
+}
+
+static crash_status upload_box_state(crash_ctx* c, int b) {
+  const crash_grid_desc& d = c->bh[b].d;
+  const BoxMeta& m = c->meta[b];
+  const size_t n = (size_t)m.ncell;
+  std::vector<float> fh;
+  std::vector<double> dh;
+  if (d.n_H) {
+    CK(cudaMemcpy(c->nH + m.cell_off, d.n_H, n * sizeof(float), cudaMemcpyHostToDevice));
+  } else {
+    fh.assign(n, (float)d.n_H0);
+    CK(cudaMemcpy(c->nH + m.cell_off, fh.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  const double* src[4] = {d.x_HII, d.x_HeII, d.x_HeIII, d.T};
+  const double uni[4] = {d.x_HII0, d.x_HeII0, d.x_HeIII0, d.T0};
+  double* dst[4] = {c->xHII, c->xHeII, c->xHeIII, c->T};
+  for (int f = 0; f < 4; ++f) {
+    if (src[f]) {
+      CK(cudaMemcpy(dst[f] + m.cell_off, src[f], n * 8, cudaMemcpyHostToDevice));
+    } else {
+      dh.assign(n, uni[f]);
+      CK(cudaMemcpy(dst[f] + m.cell_off, dh.data(), n * 8, cudaMemcpyHostToDevice));
+    }
+  }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* descs,
+                                         crash_ctx** out) {
+  crash_ctx* c = nullptr;
+  if (!out) return set_err(c, CRASH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_boxes < 1 || n_boxes > CRASH_MAX_BOXES || !descs)
+    return set_err(c, CRASH_ERR_ARG, "n_boxes must be in [1, 4096] with descriptors");
+  for (int i = 0; i < n_boxes; ++i) {
+    crash_status st = validate_desc(descs[i], i);
+    if (st != CRASH_OK) return st;
+    if (descs[i].precision != descs[0].precision)
+      return set_err(c, CRASH_ERR_ARG, "all boxes of a batch need the same precision");
+  }
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+    return set_err(c, CRASH_ERR_CUDA, "no CUDA device available");
+  cudaGetDevice(&dev);
+  c = new crash_ctx();
+  c->device = dev;
+  c->n_boxes = n_boxes;
+  c->precision = descs[0].precision;
+  c->bh.resize(n_boxes);
+  c->meta.resize(n_boxes);
+  crash_default_opts(&c->opts);
+  int64_t off = 0;
+  for (int i = 0; i < n_boxes; ++i) {
+    const crash_grid_desc& d = descs[i];
+    c->bh[i].d = d;
+    BoxMeta& m = c->meta[i];
+    memset(&m, 0, sizeof m);
+    m.nx = d.nx; m.ny = d.ny; m.nz = d.nz;
+    m.isothermal = d.isothermal ? 1 : 0;
+    m.cell_off = off;
+    m.ncell = (int64_t)d.nx * d.ny * d.nz;
+    m.dl = d.box_cm / d.nx;
+    m.he = d.he_over_h;
+    m.T_cmb = d.z_compton >= 0 ? 2.725 * (1.0 + d.z_compton) : 0.0;
+    m.seed = d.seed;
+    m.caseB = d.caseB ? 1 : 0;
+    off += m.ncell;
+    c->any_he |= d.he_over_h > 0;
+    c->any_heat |= !d.isothermal;
+  }
+  c->n_cells = off;
+  auto fail = [&](crash_status st) { release(c); return st; };
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { g_create_error = cudaGetErrorString(e); return fail(CRASH_ERR_CUDA); }
+  const size_t n = (size_t)c->n_cells;
+  struct A { void** p; size_t bytes; };
+  std::vector<A> allocs = {
+      {(void**)&c->nH, n * 4}, {(void**)&c->xHII, n * 8}, {(void**)&c->xHeII, n * 8},
+      {(void**)&c->xHeIII, n * 8}, {(void**)&c->T, n * 8}, {(void**)&c->dep, n * 32},
+      {(void**)&c->d_meta, sizeof(BoxMeta) * n_boxes},
+      {(void**)&c->budget, 64 * (size_t)n_boxes}, {(void**)&c->totals, 64 * (size_t)n_boxes},
+      {(void**)&c->step_dev, 8},
+      {(void**)&c->err, sizeof(int)}, {(void**)&c->boxE, sizeof(int) * n_boxes}};
+  if (c->precision == CRASH_MIXED) allocs.push_back({(void**)&c->abs32, n * 16});
+  else allocs.push_back({(void**)&c->abs64, n * 32});
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
+      return fail(e == cudaErrorMemoryAllocation ? CRASH_ERR_OOM : CRASH_ERR_CUDA);
+    }
+  }
+  cudaMemset(c->budget, 0, 64 * (size_t)n_boxes);
+  cudaMemset(c->totals, 0, 64 * (size_t)n_boxes);
+  cudaMemset(c->step_dev, 0, 8);
+  cudaMemset(c->err, 0, sizeof(int));
+  cudaMemset(c->dep, 0, n * 32);
+  for (int i = 0; i < n_boxes; ++i) {
+    crash_status st = upload_box_state(c, i);
+    if (st != CRASH_OK) {
+      g_create_error = c->error;
+      return fail(st);
+    }
+  }
+  *out = c;
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_init_grid(const crash_grid_desc* d, crash_ctx** out) {
+  if (!d) return set_err(nullptr, CRASH_ERR_ARG, "desc is NULL");
+  return crash_init_batch(1, d, out);
+}
+
+// ---------------------------------------------------------------- sources
+static void cross_sections(int nb, const double* E, BinTables& t, int& heatF) {
+  double emax = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    const double e = E[j];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    // hydrogenic H I and He II: sigma_0 (E_th / E)^3
+    if (e >= kEth[0]) { const double r = kEth[0] / e; s0 = 6.30e-18 * ((r * r) * r); }
+    if (e >= kEth[2]) { const double r = kEth[2] / e; s2 = 1.58e-18 * ((r * r) * r); }
+    // He I: Osterbrock (1989) fit with beta = 1.66, s = 2.05
+    if (e >= kEth[1]) {
+      const double y = e / kEth[1];
+      s1 = 7.83e-18 * (1.66 * pow(y, -2.05) + (1.0 - 1.66) * pow(y, -3.05));
+    }
+    t.sigma[0][j] = s0; t.sigma[1][j] = s1; t.sigma[2][j] = s2;
+    for (int s = 0; s < 3; ++s)
+      if (e >= kEth[s] && e - kEth[s] > emax) emax = e - kEth[s];
+  }
+  heatF = 0;
+  if (emax > 1.0) {
+    int ex;
+    double m = frexp(emax, &ex);
+    heatF = (m == 0.5) ? ex - 1 : ex;
+  }
+  for (int s = 0; s < 3; ++s)
+    for (int j = 0; j < nb; ++j) {
+      t.wheat[s][j] = E[j] >= kEth[s] ? ldexp(E[j] - kEth[s], -heatF) : 0.0;
+      t.sigma32[s][j] = (float)t.sigma[s][j];
+      t.wheat32[s][j] = (float)t.wheat[s][j];
+    }
+  t.n_bins = nb;
+}
+
+static crash_status rebuild_sources(crash_ctx* c) {
+  int total = 0;
+  for (int b = 0; b < c->n_boxes; ++b) {
+    c->meta[b].src_off = total;
+    c->meta[b].n_src = (int)c->bh[b].ndot.size();
+    total += c->meta[b].n_src;
+  }
+  const int nb = c->n_bins;
+  if (total > c->src_cap) {
+    void* old[] = {c->src_pos, c->src_ndot, c->src_frac, c->src_base, c->src_rem};
+    for (void* p : old)
+      if (p) cudaFree(p);
+    c->src_pos = c->src_ndot = c->src_frac = nullptr;
+    c->src_base = c->src_rem = nullptr;
+    CK(cudaMalloc(&c->src_pos, sizeof(double) * 3 * total));
+    CK(cudaMalloc(&c->src_ndot, sizeof(double) * total));
+    CK(cudaMalloc(&c->src_frac, sizeof(double) * total * CRASH_MAX_BINS));
+    CK(cudaMalloc(&c->src_base, sizeof(int64_t) * total * CRASH_MAX_BINS));
+    CK(cudaMalloc(&c->src_rem, sizeof(int64_t) * total * CRASH_MAX_BINS));
+    c->src_cap = total;
+  }
+  std::vector<double> pos, ndot, frac;
+  pos.reserve(3 * total); ndot.reserve(total); frac.reserve((size_t)total * nb);
+  for (int b = 0; b < c->n_boxes; ++b) {
+    const BoxHost& h = c->bh[b];
+    pos.insert(pos.end(), h.pos.begin(), h.pos.end());
+    ndot.insert(ndot.end(), h.ndot.begin(), h.ndot.end());
+    frac.insert(frac.end(), h.frac.begin(), h.frac.end());
+  }
+  c->n_src_total = total;
+  if (total) {
+    CK(cudaMemcpy(c->src_pos, pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->src_ndot, ndot.data(), ndot.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->src_frac, frac.data(), frac.size() * 8, cudaMemcpyHostToDevice));
+  }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_add_sources_box(crash_ctx* c, int box, int n_src,
+                                              const double* pos, const double* ndot,
+                                              int n_bins, const double* bin_eV,
+                                              const double* bin_frac) {
+  if (!c) return CRASH_ERR_ARG;
+  if (box < 0 || box >= c->n_boxes) return set_err(c, CRASH_ERR_ARG, "box index out of range");
+  if (n_src < 1 || !pos || !ndot || !bin_eV || !bin_frac)
+    return set_err(c, CRASH_ERR_ARG, "need n_src >= 1 and non-NULL arrays");
+  if (n_bins < 1 || n_bins > CRASH_MAX_BINS)
+    return set_err(c, CRASH_ERR_OVERFLOW, "n_bins must be in [1, 16]");
+  for (int j = 0; j < n_bins; ++j)
+    if (!(bin_eV[j] > 0)) return set_err(c, CRASH_ERR_ARG, "bin energies must be positive");
+  // all boxes share one bin table
+  bool others = false;
+  for (int b = 0; b < c->n_boxes; ++b) others |= (b != box && c->bh[b].has_sources);
+  if (others && (n_bins != c->n_bins || !std::equal(bin_eV, bin_eV + n_bins, c->bin_eV.begin())))
+    return set_err(c, CRASH_ERR_ARG, "all boxes must use the same frequency bins");
+  const crash_grid_desc& d = c->bh[box].d;
+  double mx = 0.0;
+  for (int s = 0; s < n_src; ++s) {
+    const double* p = pos + 3 * s;
+    if (!(p[0] >= 0 && p[0] < d.nx && p[1] >= 0 && p[1] < d.ny && p[2] >= 0 && p[2] < d.nz))
+      return set_err(c, CRASH_ERR_ARG, "source position outside the grid");
+    if (!(ndot[s] >= 0) || !isfinite(ndot[s]))
+      return set_err(c, CRASH_ERR_ARG, "source rates must be finite and >= 0");
+    for (int j = 0; j < n_bins; ++j)
+      if (!(bin_frac[(size_t)s * n_bins + j] >= 0))
+        return set_err(c, CRASH_ERR_ARG, "bin fractions must be >= 0");
+    mx = std::max(mx, ndot[s]);
+  }
+  BoxHost& h = c->bh[box];
+  h.pos.assign(pos, pos + 3 * n_src);
+  h.ndot.assign(ndot, ndot + n_src);
+  h.frac.assign(bin_frac, bin_frac + (size_t)n_src * n_bins);
+  h.has_sources = true;
+  c->n_bins = n_bins;
+  c->bin_eV.assign(bin_eV, bin_eV + n_bins);
+  int heatF = 0;
+  cross_sections(n_bins, bin_eV, c->tables, heatF);
+  for (int b = 0; b < c->n_boxes; ++b) c->meta[b].heatF = heatF;
+  c->meta[box].ndot_max = mx;
+  crash_status st = rebuild_sources(c);
+  if (st != CRASH_OK) return st;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_add_sources(crash_ctx* c, int n_src, const double* pos,
+                                          const double* ndot, int n_bins, const double* bin_eV,
+                                          const double* bin_frac) {
+  return crash_add_sources_box(c, 0, n_src, pos, ndot, n_bins, bin_eV, bin_frac);
+}
+
+extern "C" crash_status crash_set_options(crash_ctx* c, const crash_run_opts* o) {
+  if (!c || !o) return set_err(c, CRASH_ERR_ARG, "NULL argument");
+  if (o->pkt_end < o->pkt_begin) return set_err(c, CRASH_ERR_ARG, "pkt_end < pkt_begin");
+  if (!(o->chem_eps > 0) || o->chem_max_sub < 1)
+    return set_err(c, CRASH_ERR_ARG, "chem_eps must be > 0 and chem_max_sub >= 1");
+  if (o->block_size < 0 || o->block_size > 1024 || (o->block_size % 32))
+    return set_err(c, CRASH_ERR_ARG, "block_size must be a multiple of 32 in [0, 1024]");
+  if (o->seg_per_iter < 0) return set_err(c, CRASH_ERR_ARG, "seg_per_iter must be >= 0");
+  c->opts = *o;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_set_step_index(crash_ctx* c, uint64_t step) {
+  if (!c) return CRASH_ERR_ARG;
+  cudaSetDevice(c->device);
+  unsigned long long v = step;
+  CK(cudaMemcpyAsync(c->step_dev, &v, 8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->step_host = step;
+  return CRASH_OK;
+}
+
+// ---------------------------------------------------------------- step
+// end of step: advance the step index and add the step's budget to the totals
+__global__ void k_end_step(unsigned long long* s, const unsigned long long* budget,
+                           unsigned long long* totals, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *s += 1ull;
+  if (i < 8 * n) {
+    int k = i & 7;
+    if (k == 5 || k == 6) totals[i] = budget[i];
+    else totals[i] += budget[i];
+  }
+}
+
+static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
+  StepArgs a;
+  memset(&a, 0, sizeof a);
+  a.boxes = c->d_meta;
+  a.n_boxes = c->n_boxes;
+  a.step_dev = c->step_dev;
+  a.dt = dt;
+  a.total_packets = total;
+  a.src_pos = c->src_pos; a.src_ndot = c->src_ndot; a.src_frac = c->src_frac;
+  a.src_base = c->src_base; a.src_rem = c->src_rem;
+  a.box_E = c->boxE;
+  a.n_src_total = c->n_src_total;
+  a.nH = c->nH; a.xHII = c->xHII; a.xHeII = c->xHeII; a.xHeIII = c->xHeIII; a.T = c->T;
+  a.abs64 = c->abs64; a.abs32 = c->abs32; a.dep = c->dep;
+  a.n_cells_total = c->n_cells;
+  a.budget = c->budget;
+  a.err = c->err;
+  a.any_he = c->any_he; a.any_heat = c->any_heat;
+  a.chemistry = c->opts.chemistry;
+  a.chem_eps = c->opts.chem_eps;
+  a.chem_max_sub = c->opts.chem_max_sub;
+  a.cool_mask = c->opts.cool_mask;
+  return a;
+}
+
+// the launch sequence of one step (everything on c->stream)
+static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, int64_t* nk) {
+  CK(cudaMemsetAsync(c->budget, 0, 64 * (size_t)c->n_boxes, c->stream));
+  launch_prep(a, c->precision, c->stream);
+  launch_budget(a, c->tables, c->stream);
+  *nk = 3 + (c->opts.chemistry ? 1 : 0);   // prep, budget, end-of-step, chemistry
+  if (c->precision == CRASH_MIXED) {
+    int rc = launch_trace_mixed(a, c->tables, c->opts, c->wf, c->stream,
+                                timing ? &c->events : nullptr, &c->ev_used);
+    if (rc < 0) return set_err(c, CRASH_ERR_CUDA, "mixed transport launch failed");
+    *nk += rc;
+  } else {
+    *nk += 1;
+    if (timing) {
+      if (c->ev_used >= (int)c->events.size()) {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        c->events.push_back({e0, e1});
+      }
+      CK(cudaEventRecord(c->events[c->ev_used].first, c->stream));
+    }
+    launch_trace_fp64(a, c->tables, c->opts.block_size, c->stream);
+    if (timing) {
+      CK(cudaEventRecord(c->events[c->ev_used].second, c->stream));
+      c->ev_used++;
+    }
+  }
+  if (c->opts.chemistry) launch_chemistry(a, c->stream);
+  k_end_step<<<(8 * c->n_boxes + 255) / 256, 256, 0, c->stream>>>(c->step_dev, c->budget,
+                                                                    c->totals, c->n_boxes);
+  CK(cudaGetLastError());
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t* P) {
+  if (!c) return CRASH_ERR_ARG;
+  if (!(dt > 0) || !isfinite(dt)) return set_err(c, CRASH_ERR_ARG, "dt must be positive");
+  if (!P) return set_err(c, CRASH_ERR_ARG, "packets_per_box is NULL");
+  cudaSetDevice(c->device);
+  int64_t total = 0;
+  std::vector<uint64_t> key = {(uint64_t)c->n_boxes};
+  {
+    uint64_t dtb;
+    memcpy(&dtb, &dt, 8);
+    key.push_back(dtb);
+  }
+  for (int b = 0; b < c->n_boxes; ++b) {
+    if (!c->bh[b].has_sources) return set_err(c, CRASH_ERR_STATE, "a box has no sources");
+    BoxMeta& m = c->meta[b];
+    if (P[b] == 0 || P[b] % (uint64_t)m.n_src)
+      return set_err(c, CRASH_ERR_ARG, "packets_per_step must be a positive multiple of n_src");
+    const uint64_t Ns = P[b] / (uint64_t)m.n_src;
+    if (Ns > 0xFFFFFFFFull) return set_err(c, CRASH_ERR_OVERFLOW, "more than 2^32-1 packets per source");
+    m.pkts_per_src = Ns;
+    m.win_lo = (uint32_t)std::min<uint64_t>(c->opts.pkt_begin, Ns);
+    m.win_hi = (uint32_t)std::min<uint64_t>(c->opts.pkt_end, Ns);
+    if (m.win_hi < m.win_lo) m.win_hi = m.win_lo;
+    m.pkt_off = total;
+    m.pkt_count = (int64_t)m.n_src * (int64_t)(m.win_hi - m.win_lo);
+    total += m.pkt_count;
+    key.push_back(P[b]);
+  }
+  if (total > ((int64_t)1 << 40)) return set_err(c, CRASH_ERR_OVERFLOW, "too many packets in one step");
+  CK(cudaMemcpyAsync(c->d_meta, c->meta.data(), sizeof(BoxMeta) * c->n_boxes,
+                     cudaMemcpyHostToDevice, c->stream));
+  if (c->precision == CRASH_MIXED && !c->wf) {
+    int st = 0;
+    c->wf = wavefront_create(std::min<int64_t>(total, (int64_t)1 << 26), c->n_cells, c->n_bins, &st);
+    if (!c->wf) return set_err(c, CRASH_ERR_OOM, "wavefront workspace allocation failed");
+  }
+  StepArgs a = make_args(c, dt, total);
+  const bool timing = c->opts.timing != 0;
+  crash_status st;
+  if (c->opts.use_graph && !timing) {
+    if (!c->graph || c->graph_key != key) {
+      if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      st = enqueue_step(c, a, false, &c->graph_launches);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+      if (st != CRASH_OK) return st;
+      if (e != cudaSuccess) return set_err(c, CRASH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return set_err(c, CRASH_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      c->graph_key = key;
+    }
+    CK(cudaGraphLaunch(c->graph, c->stream));
+    c->launches += c->graph_launches;
+  } else {
+    int64_t nk = 0;
+    st = enqueue_step(c, a, timing, &nk);
+    if (st != CRASH_OK) return st;
+    c->launches += nk;
+  }
+  c->step_host += 1;
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_step(crash_ctx* c, double dt, uint64_t P) {
+  if (!c) return CRASH_ERR_ARG;
+  if (c->n_boxes != 1) return set_err(c, CRASH_ERR_ARG, "batched context: use crash_step_batch");
+  return crash_step_batch(c, dt, &P);
+}
+
+static crash_status check_device_error(crash_ctx* c) {
+  int e = 0;
+  CK(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    std::string m = "device-side limit hit:";
+    if (e & ERR_DDA_LIMIT) m += " DDA iteration limit;";
+    if (e & ERR_DIRECTION) m += " direction sampling exceeded 64 attempts;";
+    if (e & ERR_QUEUE) m += " packet queue overflow;";
+    if (e & ERR_WATCHDOG) m += " wavefront pass limit;";
+    return set_err(c, CRASH_ERR_TIMEOUT, m);
+  }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_sync(crash_ctx* c) {
+  if (!c) return CRASH_ERR_ARG;
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+// ---------------------------------------------------------------- fields
+extern "C" crash_status crash_read_fields_box(crash_ctx* c, int box, int f, void* out) {
+  if (!c) return CRASH_ERR_ARG;
+  if (!out) return set_err(c, CRASH_ERR_ARG, "output is NULL");
+  if (box < 0 || box >= c->n_boxes) return set_err(c, CRASH_ERR_ARG, "box index out of range");
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  crash_status st = check_device_error(c);
+  if (st != CRASH_OK) return st;
+  const BoxMeta& m = c->meta[box];
+  const size_t n = (size_t)m.ncell;
+  switch (f) {
+    case CRASH_F_XHII: CK(cudaMemcpy(out, c->xHII + m.cell_off, n * 8, cudaMemcpyDeviceToHost)); break;
+    case CRASH_F_XHEII: CK(cudaMemcpy(out, c->xHeII + m.cell_off, n * 8, cudaMemcpyDeviceToHost)); break;
+    case CRASH_F_XHEIII: CK(cudaMemcpy(out, c->xHeIII + m.cell_off, n * 8, cudaMemcpyDeviceToHost)); break;
+    case CRASH_F_T: CK(cudaMemcpy(out, c->T + m.cell_off, n * 8, cudaMemcpyDeviceToHost)); break;
+    case CRASH_F_DEP_HI: case CRASH_F_DEP_HEI: case CRASH_F_DEP_HEII: case CRASH_F_DEP_E:
+      CK(cudaMemcpy2D(out, 8, c->dep + 4 * m.cell_off + (f - CRASH_F_DEP_HI), 32, 8, n,
+                      cudaMemcpyDeviceToHost));
+      break;
+    case CRASH_F_BUDGET: CK(cudaMemcpy(out, c->budget + 8 * box, 64, cudaMemcpyDeviceToHost)); break;
+    case CRASH_F_TOTALS: CK(cudaMemcpy(out, c->totals + 8 * box, 64, cudaMemcpyDeviceToHost)); break;
+    case CRASH_F_NH: {
+      std::vector<float> tmp(n);
+      CK(cudaMemcpy(tmp.data(), c->nH + m.cell_off, n * 4, cudaMemcpyDeviceToHost));
+      double* o = (double*)out;
+      for (size_t i = 0; i < n; ++i) o[i] = (double)tmp[i];
+      break;
+    }
+    default: return set_err(c, CRASH_ERR_ARG, "unknown field id");
+  }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_read_fields(crash_ctx* c, int f, void* out) {
+  return crash_read_fields_box(c, 0, f, out);
+}
+
+extern "C" crash_status crash_write_fields_box(crash_ctx* c, int box, int f, const void* in) {
+  if (!c) return CRASH_ERR_ARG;
+  if (!in) return set_err(c, CRASH_ERR_ARG, "input is NULL");
+  if (box < 0 || box >= c->n_boxes) return set_err(c, CRASH_ERR_ARG, "box index out of range");
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  const BoxMeta& m = c->meta[box];
+  const size_t n = (size_t)m.ncell;
+  double* dst = nullptr;
+  switch (f) {
+    case CRASH_F_XHII: dst = c->xHII; break;
+    case CRASH_F_XHEII: dst = c->xHeII; break;
+    case CRASH_F_XHEIII: dst = c->xHeIII; break;
+    case CRASH_F_T: dst = c->T; break;
+    default: return set_err(c, CRASH_ERR_ARG, "field is not writable");
+  }
+  CK(cudaMemcpy(dst + m.cell_off, in, n * 8, cudaMemcpyHostToDevice));
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_write_fields(crash_ctx* c, int f, const void* in) {
+  return crash_write_fields_box(c, 0, f, in);
+}
+
+// ---------------------------------------------------------------- timing
+extern "C" crash_status crash_kernel_time(crash_ctx* c, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return set_err(c, CRASH_ERR_ARG, "NULL argument");
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  double acc = c->ms_accum;
+  for (int i = 0; i < c->ev_used; ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->events[i].first, c->events[i].second));
+    acc += t;
+  }
+  c->ms_accum = acc;
+  c->launches_accum += c->ev_used;
+  c->ev_used = 0;
+  *ms = c->ms_accum;
+  *launches = c->launches_accum;
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_reset_kernel_time(crash_ctx* c) {
+  if (!c) return CRASH_ERR_ARG;
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  c->ev_used = 0;
+  c->ms_accum = 0.0;
+  c->launches_accum = 0;
+  return CRASH_OK;
+}
+
+// ---------------------------------------------------------------- autotune
+extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* P, int* block,
+                                       int* seg, int* resort) {
+  if (!c || !P) return CRASH_ERR_ARG;
+  cudaSetDevice(c->device);
+  // save the state and the step index so that trials leave no trace
+  const size_t n = (size_t)c->n_cells;
+  double* save = nullptr;
+  CK(cudaMalloc(&save, n * 8 * 4));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(save, c->xHII, n * 8, cudaMemcpyDeviceToDevice));
+  CK(cudaMemcpy(save + n, c->xHeII, n * 8, cudaMemcpyDeviceToDevice));
+  CK(cudaMemcpy(save + 2 * n, c->xHeIII, n * 8, cudaMemcpyDeviceToDevice));
+  CK(cudaMemcpy(save + 3 * n, c->T, n * 8, cudaMemcpyDeviceToDevice));
+  unsigned long long step0 = 0;
+  CK(cudaMemcpy(&step0, c->step_dev, 8, cudaMemcpyDeviceToHost));
+  crash_run_opts base = c->opts;
+  crash_run_opts best = base;
+  double best_ms = 1e300;
+  std::vector<int> blocks = {64, 128, 256};
+  std::vector<int> segs = {0};
+  std::vector<int> resorts = {0};
+  if (c->precision == CRASH_MIXED) {
+    segs = {16, 32, 64, 128};
+    resorts = {-1, 1, 2, 4};
+  }
+  crash_status st = CRASH_OK;
+  for (int bs : blocks)
+    for (int sg : segs)
+      for (int rs : resorts) {
+        crash_run_opts o = base;
+        o.block_size = bs;
+        o.seg_per_iter = sg;
+        o.resort_interval = rs;
+        o.chemistry = 0;
+        o.use_graph = 0;
+        o.timing = 0;
+        c->opts = o;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        st = crash_step_batch(c, dt, P);                 // warm-up
+        if (st == CRASH_OK) {
+          cudaEventRecord(e0, c->stream);
+          st = crash_step_batch(c, dt, P);
+          cudaEventRecord(e1, c->stream);
+        }
+        cudaStreamSynchronize(c->stream);
+        float ms = 0.f;
+        if (st == CRASH_OK) cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != CRASH_OK) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = base;
+          best.block_size = bs;
+          best.seg_per_iter = sg;
+          best.resort_interval = rs;
+        }
+      }
+  c->opts = best;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  cudaMemcpy(c->xHII, save, n * 8, cudaMemcpyDeviceToDevice);
+  cudaMemcpy(c->xHeII, save + n, n * 8, cudaMemcpyDeviceToDevice);
+  cudaMemcpy(c->xHeIII, save + 2 * n, n * 8, cudaMemcpyDeviceToDevice);
+  cudaMemcpy(c->T, save + 3 * n, n * 8, cudaMemcpyDeviceToDevice);
+  cudaMemcpy(c->step_dev, &step0, 8, cudaMemcpyHostToDevice);
+  cudaFree(save);
+  c->step_host = step0;
+  if (st != CRASH_OK) return st;
+  if (block) *block = best.block_size;
+  if (seg) *seg = best.seg_per_iter;
+  if (resort) *resort = best.resort_interval;
+  return CRASH_OK;
+}

@@ -1,0 +1,102 @@
+// crash_internal.cuh -- device data layout and kernel interfaces shared by
+// the CUDA translation units of libcrash (not part of the public ABI).
+//
+// HBM layout (all boxes of a batch concatenated, x fastest inside a box):
+//   nH      float  [cells]          hydrogen density (static input)
+//   x_HII, x_HeII, x_HeIII, T  double [cells]  state (SoA, coalesced per-cell kernels)
+//   abs64   double4-like [cells]    n_HI, n_HeI, n_HeII, 0 frozen per step (FP64 form)
+//   abs32   float4  [cells]         the same in FP32 (mixed form)
+//   dep     int64 x4 [cells]        dep_HI, dep_HeI, dep_HeII, dep_E (one 32-byte sector per cell)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/crash.h"
+
+#define CRASH_MAX_BINS 16
+#define CRASH_MAX_BOXES 4096
+
+// Per-box constants (uploaded when sources or per-step plans change).
+struct BoxMeta {
+  int nx, ny, nz;
+  int isothermal;
+  int64_t cell_off;    // first cell of the box in the concatenated arrays
+  int64_t ncell;
+  double dl;           // cell edge, cm
+  double he;           // n_He / n_H
+  double T_cmb;        // 0 => Compton off
+  uint64_t seed;
+  int caseB;
+  int src_off;         // sources [src_off, src_off + n_src)
+  int n_src;
+  int heatF;           // heat unit 2^heatF eV (per photon quantum)
+  double ndot_max;     // max photon rate over the box's sources
+  // per-step packet plan
+  uint64_t pkts_per_src;   // N_s = packets_per_step / n_src
+  uint32_t win_lo, win_hi; // traced packet ids [win_lo, win_hi) per source
+  int64_t pkt_off;         // first global packet slot of this box in the launch
+  int64_t pkt_count;       // n_src * (win_hi - win_lo)
+};
+
+// Cross sections and heating weights per species and bin (passed by value;
+// kernel parameters live in the constant bank).
+struct BinTables {
+  int n_bins;
+  double sigma[3][CRASH_MAX_BINS];   // cm^2
+  double wheat[3][CRASH_MAX_BINS];   // (E_j - E_th,s) / 2^F, or 0 below threshold
+  float sigma32[3][CRASH_MAX_BINS];
+  float wheat32[3][CRASH_MAX_BINS];
+};
+
+struct StepArgs {
+  const BoxMeta* boxes;
+  int n_boxes;
+  unsigned long long* step_dev;   // step index (Philox counter word), advanced on the device
+  double dt;
+  int64_t total_packets;
+  // sources
+  const double* src_pos;     // [n_src_total][3]
+  const double* src_ndot;    // [n_src_total]
+  const double* src_frac;    // [n_src_total][n_bins]
+  int64_t* src_base;         // [n_src_total][n_bins]  per-packet content base (written per step)
+  int64_t* src_rem;          // [n_src_total][n_bins]  packets p < rem get one more quantum
+  int* box_E;                // [n_boxes] photon quantum exponent this step
+  int n_src_total;
+  // grid
+  const float* nH;
+  double* xHII; double* xHeII; double* xHeIII; double* T;
+  double* abs64;             // [cells][4]
+  float* abs32;              // [cells][4]
+  unsigned long long* dep;   // [cells][4]
+  int64_t n_cells_total;
+  // budget [n_boxes][8] and device error word
+  unsigned long long* budget;
+  int* err;
+  // options
+  int any_he;                // some box has helium (selects the H+He kernels)
+  int any_heat;              // some box evolves T (selects the heating deposit)
+  int chemistry;
+  double chem_eps;
+  int chem_max_sub;
+  int cool_mask;
+};
+
+// device error bits
+enum { ERR_DDA_LIMIT = 1, ERR_DIRECTION = 2, ERR_QUEUE = 4, ERR_WATCHDOG = 8 };
+
+// launchers implemented in the kernel translation units
+void launch_prep(const StepArgs& a, int precision, cudaStream_t s);
+void launch_budget(const StepArgs& a, const BinTables& t, cudaStream_t s);
+void launch_trace_fp64(const StepArgs& a, const BinTables& t, int block, cudaStream_t s);
+void launch_chemistry(const StepArgs& a, cudaStream_t s);
+int launch_trace_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o,
+                       void* wf_state, cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev,
+                       int* ev_used);
+
+// wavefront workspace (mixed form)
+void* wavefront_create(int64_t max_packets, int64_t n_cells_total, int n_bins, int* status);
+void wavefront_destroy(void* w);
+int64_t wavefront_capacity(void* w);

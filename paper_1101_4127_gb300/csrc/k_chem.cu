@@ -1,0 +1,269 @@
+// k_chem.cu -- per-cell ionisation network and temperature update (FP64),
+// one thread per cell over all boxes, reading the step's integer deposits.
+//
+// Sec. 2: each cell's ionisation fractions change by photo-ionisation (the
+// absorbed photons), collisional ionisation and recombination, and its
+// temperature by photo-heating, the change in the number of free particles
+// and the continuous processes (bremsstrahlung, Compton, collisional
+// ionisation and excitation cooling, recombination cooling).  Sec. 3.2: the
+// network is sub-sampled when the step exceeds its time-scales.
+//
+// Coupling of transport to chemistry (step-synchronous form): the step's
+// deposit of species s, dep_s quanta of 2^E photons, defines a
+// photo-ionisation rate per absorber Gamma_s = dep_s 2^E / (dt n_s^0 V) with
+// n_s^0 the absorber density frozen at the start of the step; photo-heating
+// is the mean excess energy per absorbed photon times the photo-ionisation
+// rate of the current absorbers.
+//
+// Integrator per sub-step h (h limited so that no ionic fraction changes by
+// more than eps * max(x, 1e-3) and T by more than eps * T; the last allowed
+// sub-step takes what remains):
+//   * backward Euler for the H (2-state) and He (3-state tridiagonal) chains
+//     at fixed T, with n_e at the end of the sub-step by 4 fixed-point passes;
+//   * fractions clamped to [0,1], He renormalised to unit sum;
+//   * 1.5 k (n_tot T)_new = 1.5 k (n_tot T)_old + h (H + C n_e T_cmb)
+//     - h (Lambda(T_old)/T_old + C n_e) T_new  (cooling linear in T_new).
+#include <math.h>
+
+#include "crash_internal.cuh"
+#include "k_device.cuh"
+
+using namespace crash;
+
+namespace {
+
+constexpr double kB = 1.380649e-16;
+constexpr double eV = 1.602176634e-12;
+constexpr double sigmaT = 6.6524587321e-25;
+constexpr double aRad = 7.565723e-15;
+constexpr double mE = 9.1093837015e-28;
+constexpr double cLight = 2.99792458e10;
+
+struct Rates {
+  double aHII, aHeII, aHeIII, adiel;     // recombination, cm^3/s
+  double bHI, bHeI, bHeII;               // collisional ionisation, cm^3/s
+  double cexHI, cexHeII;                 // collisional excitation cooling, erg cm^3/s
+  double cionHI, cionHeI, cionHeII;      // collisional ionisation cooling
+  double crecHII, crecHeII, crecHeIII;   // recombination cooling
+  double cdiel;                          // dielectronic recombination cooling
+  double cff;                            // bremsstrahlung per Z^2 (times n_e n_i)
+};
+
+// Hui & Gnedin (1997) recombination (case A/B) and recombination cooling;
+// Cen (1992) collisional ionisation, collisional excitation cooling and
+// dielectronic recombination; bremsstrahlung 1.42e-27 g_ff sqrt(T).
+__device__ Rates rates_at(double T, int caseB) {
+  Rates r;
+  const double lH = 315614.0 / T, lHe1 = 570670.0 / T, lHe2 = 1263030.0 / T;
+  const double sq = 1.0 / (1.0 + sqrt(T / 1e5));
+  if (caseB) {
+    r.aHII = 2.753e-14 * pow(lH, 1.5) / pow(1.0 + pow(lH / 2.740, 0.407), 2.242);
+    r.aHeII = 1.26e-14 * pow(lHe1, 0.750);
+    r.aHeIII = 2.0 * 2.753e-14 * pow(lHe2, 1.5) / pow(1.0 + pow(lHe2 / 2.740, 0.407), 2.242);
+    r.crecHII = 3.435e-30 * T * pow(lH, 1.970) / pow(1.0 + pow(lH / 2.250, 0.376), 3.720);
+    r.crecHeIII = 8.0 * 3.435e-30 * (0.25 * T) * pow(lHe2, 1.970) /
+                  pow(1.0 + pow(lHe2 / 2.250, 0.376), 3.720);
+  } else {
+    r.aHII = 1.269e-13 * pow(lH, 1.503) / pow(1.0 + pow(lH / 0.522, 0.470), 1.923);
+    r.aHeII = 3.0e-14 * pow(lHe1, 0.654);
+    r.aHeIII = 2.0 * 1.269e-13 * pow(lHe2, 1.503) / pow(1.0 + pow(lHe2 / 0.522, 0.470), 1.923);
+    r.crecHII = 1.778e-29 * T * pow(lH, 1.965) / pow(1.0 + pow(lH / 0.541, 0.502), 2.697);
+    r.crecHeIII = 8.0 * 1.778e-29 * (0.25 * T) * pow(lHe2, 1.965) /
+                  pow(1.0 + pow(lHe2 / 0.541, 0.502), 2.697);
+  }
+  r.adiel = 1.90e-3 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T));
+  const double rt = sqrt(T);
+  r.bHI = 5.85e-11 * rt * exp(-157809.1 / T) * sq;
+  r.bHeI = 2.38e-11 * rt * exp(-285335.4 / T) * sq;
+  r.bHeII = 5.68e-12 * rt * exp(-631515.0 / T) * sq;
+  const double lg = log10(T);
+  const double gff = 1.1 + 0.34 * exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
+  r.cexHI = 7.50e-19 * exp(-118348.0 / T) * sq;
+  r.cexHeII = 5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) * sq;
+  r.cionHI = 13.6 * eV * r.bHI;
+  r.cionHeI = 24.6 * eV * r.bHeI;
+  r.cionHeII = 54.4 * eV * r.bHeII;
+  r.crecHeII = kB * T * r.aHeII;
+  r.cdiel = 6.526e-11 * r.adiel;
+  r.cff = 1.42e-27 * gff * rt;
+  return r;
+}
+
+__device__ __forceinline__ double cooling_rate(const Rates& r, int mask, double ne, double nHI,
+                                               double nHII, double nHeI, double nHeII,
+                                               double nHeIII) {
+  double L = 0.0;
+  if (mask & 1) L += ne * (r.cexHI * nHI + r.cexHeII * nHeII);
+  if (mask & 2) L += ne * (r.cionHI * nHI + r.cionHeI * nHeI + r.cionHeII * nHeII);
+  if (mask & 4) L += ne * (r.crecHII * nHII + r.crecHeII * nHeII + r.crecHeIII * nHeIII);
+  if (mask & 32) L += ne * r.cdiel * nHeII;
+  if (mask & 8) L += ne * r.cff * (nHII + nHeII + 4.0 * nHeIII);
+  return L;
+}
+
+struct CellIn {
+  double nH, nHe, GH, G1, G2, eps_heat, Tcmb, ccomp, eps;
+  int iso, caseB, mask, max_sub;
+};
+
+// returns sub-steps; updates x (HII), y2 (HeII), y3 (HeIII), T
+__device__ int integrate_cell(const CellIn& c, double dt, double& x, double& y2, double& y3,
+                              double& T) {
+  const bool coll = (c.mask & 2) != 0, rec = (c.mask & 4) != 0, diel = (c.mask & 32) != 0;
+  const bool he = c.nHe > 0.0;
+  double rem = dt;
+  int nsub = 0;
+  while (rem > 0.0) {
+    const Rates r = rates_at(T, c.caseB);
+    const double aH = rec ? r.aHII : 0.0;
+    const double aHe2 = rec ? r.aHeII + (diel ? r.adiel : 0.0) : 0.0;
+    const double aHe3 = rec ? r.aHeIII : 0.0;
+    const double bH = coll ? r.bHI : 0.0, bHe1 = coll ? r.bHeI : 0.0, bHe2 = coll ? r.bHeII : 0.0;
+    const double y1 = (1.0 - y2) - y3;
+    const double ne = c.nH * x + c.nHe * (y2 + 2.0 * y3);
+    // rates of change at the start of the sub-step (for the step size)
+    const double IH = c.GH + bH * ne, RH = aH * ne;
+    const double I1 = c.G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = c.G2 + bHe2 * ne, R3 = aHe3 * ne;
+    const double dx = IH * (1.0 - x) - RH * x;
+    const double dy1 = -I1 * y1 + R2 * y2;
+    const double dy3 = I2 * y2 - R3 * y3;
+    const double dy2 = -dy1 - dy3;
+    double h = rem;
+    {
+      const double val[5] = {1.0 - x, x, y1, y2, y3};
+      const double der[5] = {-dx, dx, dy1, dy2, dy3};
+      const int nv = he ? 5 : 2;
+      for (int i = 0; i < nv; ++i) {
+        const double fl = val[i] > 1e-3 ? val[i] : 1e-3;
+        const double ad = fabs(der[i]);
+        if (ad * h > c.eps * fl) h = c.eps * fl / ad;
+      }
+    }
+    const double ntot = c.nH + c.nHe + ne;
+    if (!c.iso) {
+      const double nHI = c.nH * (1.0 - x), nHII = c.nH * x;
+      const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2);
+      const double L = cooling_rate(r, c.mask, ne, nHI, nHII, c.nHe * y1, c.nHe * y2, c.nHe * y3) +
+                       c.ccomp * ne * (T - c.Tcmb);
+      const double dne = c.nH * dx + c.nHe * (dy2 + 2.0 * dy3);
+      const double dT = ((heat - L) / (1.5 * kB) - T * dne) / ntot;
+      const double adT = fabs(dT);
+      if (adT * h > c.eps * T) h = c.eps * T / adT;
+    }
+    if (nsub == c.max_sub - 1 || !(h < rem)) h = rem;
+    // implicit ionisation update
+    double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+      const double ih = c.GH + bH * nen, rh = aH * nen;
+      xn = (x + h * ih) / (1.0 + h * (ih + rh));
+      if (he) {
+        const double i1 = c.G1 + bHe1 * nen, r2 = aHe2 * nen;
+        const double i2 = c.G2 + bHe2 * nen, r3 = aHe3 * nen;
+        // tridiagonal (I - h Q) y_new = y_old, Thomas elimination
+        const double a11 = 1.0 + h * i1, a12 = -h * r2;
+        const double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
+        const double a32 = -h * i2, a33 = 1.0 + h * r3;
+        const double c1 = a12 / a11, d1 = y1 / a11;
+        const double m2 = a22 - a21 * c1;
+        const double c2 = a23 / m2, d2 = (y2 - a21 * d1) / m2;
+        const double m3 = a33 - a32 * c2;
+        y3n = (y3 - a32 * d2) / m3;
+        y2n = d2 - c2 * y3n;
+        y1n = d1 - c1 * y2n;
+      }
+      nen = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
+    }
+    xn = fmin(fmax(xn, 0.0), 1.0);
+    if (he) {
+      y1n = fmax(y1n, 0.0);
+      y2n = fmax(y2n, 0.0);
+      y3n = fmax(y3n, 0.0);
+      const double s = (y1n + y2n) + y3n;
+      y2n = y2n / s;
+      y3n = y3n / s;
+      y1n = (1.0 - y2n) - y3n;
+    }
+    const double ne2 = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
+    if (!c.iso) {
+      const double nHI = c.nH * (1.0 - xn), nHII = c.nH * xn;
+      const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n);
+      const double L = cooling_rate(r, c.mask, ne2, nHI, nHII, c.nHe * y1n, c.nHe * y2n,
+                                    c.nHe * y3n);
+      const double L1 = L / T;
+      const double Cc = c.ccomp * ne2;
+      const double ntot2 = c.nH + c.nHe + ne2;
+      T = (1.5 * kB * ntot * T + h * (heat + Cc * c.Tcmb)) / (1.5 * kB * ntot2 + h * (L1 + Cc));
+    }
+    x = xn;
+    y2 = y2n;
+    y3 = y3n;
+    rem = (h == rem) ? 0.0 : rem - h;
+    ++nsub;
+  }
+  return nsub;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) k_chemistry(StepArgs a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long subs = 0;
+  int b = -1;
+  if (i < a.n_cells_total) {
+    b = box_of_cell(a.boxes, a.n_boxes, i);
+    const BoxMeta* M = a.boxes + b;
+    const int E = a.box_E[b];
+    const double q = ldexp(1.0, E);
+    const double qE = ldexp(1.0, E + M->heatF) * eV;
+    const double V = (M->dl * M->dl) * M->dl;
+    double x = a.xHII[i], y2 = a.xHeII[i], y3 = a.xHeIII[i], T = a.T[i];
+    CellIn c;
+    c.nH = (double)a.nH[i];
+    c.nHe = c.nH * M->he;
+    const double NHI = (c.nH * (1.0 - x)) * V;
+    const double NHeI = (c.nHe * ((1.0 - y2) - y3)) * V;
+    const double NHeII = (c.nHe * y2) * V;
+    const ulonglong2 d01 = reinterpret_cast<const ulonglong2*>(a.dep)[2 * i];
+    const ulonglong2 d23 = reinterpret_cast<const ulonglong2*>(a.dep)[2 * i + 1];
+    const long long dHI = (long long)d01.x, dHeI = (long long)d01.y;
+    const long long dHeII = (long long)d23.x, dE = (long long)d23.y;
+    c.GH = NHI > 0 ? ((double)dHI * q) / (a.dt * NHI) : 0.0;
+    c.G1 = NHeI > 0 ? ((double)dHeI * q) / (a.dt * NHeI) : 0.0;
+    c.G2 = NHeII > 0 ? ((double)dHeII * q) / (a.dt * NHeII) : 0.0;
+    const long long nabs = (dHI + dHeI) + dHeII;
+    c.eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
+    c.iso = M->isothermal;
+    c.caseB = M->caseB;
+    c.Tcmb = M->T_cmb;
+    c.mask = a.cool_mask;
+    if (M->T_cmb > 0 && (a.cool_mask & 16)) {
+      const double t2 = M->T_cmb * M->T_cmb;
+      c.ccomp = 4.0 * sigmaT * aRad * (t2 * t2) * kB / (mE * cLight);
+    } else {
+      c.ccomp = 0.0;
+    }
+    c.eps = a.chem_eps;
+    c.max_sub = a.chem_max_sub;
+    subs = (unsigned long long)integrate_cell(c, a.dt, x, y2, y3, T);
+    a.xHII[i] = x;
+    a.xHeII[i] = y2;
+    a.xHeIII[i] = y3;
+    a.T[i] = T;
+  }
+  // sub-step tally per box (warp sum when the warp's cells share a box)
+  int b0 = __shfl_sync(0xFFFFFFFFu, b, 0);
+  bool uniform = __all_sync(0xFFFFFFFFu, b == b0 || b < 0);
+  if (uniform) {
+    subs = warp_sum_u64(subs);
+    if ((threadIdx.x & 31) == 0 && b0 >= 0 && subs) atomicAdd(a.budget + b0 * 8 + 7, subs);
+  } else if (b >= 0) {
+    atomicAdd(a.budget + b * 8 + 7, subs);
+  }
+}
+
+void launch_chemistry(const StepArgs& a, cudaStream_t s) {
+  if (a.n_cells_total <= 0) return;
+  int64_t blocks = (a.n_cells_total + 127) / 128;
+  k_chemistry<<<(unsigned)blocks, 128, 0, s>>>(a);
+}

@@ -1,0 +1,127 @@
+// k_device.cuh -- device building blocks of the transport kernels:
+// counter-based random numbers, isotropic directions, exp(-tau) and the box
+// lookup of a packet or a cell.  Every routine here is specified down to the
+// order of its floating-point operations so that the FP64 form reproduces
+// the FP64 specification bit for bit (the translation units that include it
+// for the FP64 form are compiled with -fmad=false).
+#pragma once
+#include <stdint.h>
+
+#include "crash_internal.cuh"
+
+namespace crash {
+
+// ---------------------------------------------------------------- Philox
+// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of two
+// 32x32->64 multiplications whose high halves are xored with the other two
+// counter words and the round key; the key advances by the golden-ratio and
+// sqrt(3)-1 Weyl increments.
+struct PhiloxKey { uint32_t k0, k1; };
+
+__device__ __forceinline__ uint4 philox_round(uint4 c, PhiloxKey k) {
+  const uint32_t mA = 0xD2511F53u, mB = 0xCD9E8D57u;
+  uint32_t hiA = __umulhi(mA, c.x), loA = mA * c.x;
+  uint32_t hiB = __umulhi(mB, c.z), loB = mB * c.z;
+  return make_uint4(hiB ^ c.y ^ k.k0, loB, hiA ^ c.w ^ k.k1, loA);
+}
+
+__device__ __forceinline__ uint4 philox10(uint4 ctr, uint64_t seed) {
+  PhiloxKey k{(uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32)};
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    ctr = philox_round(ctr, k);
+    k.k0 += 0x9E3779B9u;
+    k.k1 += 0xBB67AE85u;
+  }
+  return ctr;
+}
+
+// 53-bit uniform in [0, 1) from two 32-bit words (hi word more significant)
+__device__ __forceinline__ double uniform53(uint32_t lo, uint32_t hi) {
+  unsigned long long w = ((unsigned long long)hi << 32) | (unsigned long long)lo;
+  return (double)(w >> 11) * 1.1102230246251565404236316680908203125e-16;  // 2^-53
+}
+
+// Isotropic unit vector by Marsaglia's rejection (Ann. Math. Stat. 1972):
+// (v1, v2) uniform on [-1,1)^2 accepted when 0 < s = v1^2 + v2^2 < 1, then
+// (2 v1 sqrt(1-s), 2 v2 sqrt(1-s), 1 - 2s).  Attempt a draws Philox counter
+// (pkt, src, step, a).  Returns false after 64 rejected attempts.
+__device__ __forceinline__ bool iso_direction(uint64_t seed, uint32_t step, uint32_t src,
+                                              uint32_t pkt, double& dx, double& dy, double& dz) {
+  for (uint32_t a = 0; a < 64u; ++a) {
+    uint4 r = philox10(make_uint4(pkt, src, step, a), seed);
+    double v1 = 2.0 * uniform53(r.x, r.y) - 1.0;
+    double v2 = 2.0 * uniform53(r.z, r.w) - 1.0;
+    double s = v1 * v1 + v2 * v2;
+    if (s < 1.0 && s != 0.0) {
+      double root = sqrt(1.0 - s);
+      dx = (2.0 * v1) * root;
+      dy = (2.0 * v2) * root;
+      dz = 1.0 - 2.0 * s;
+      return true;
+    }
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- exp(-tau)
+// e^-tau, tau >= 0: split -tau = k ln2 + r (Cody & Waite 1980 two-constant
+// reduction, ln2 high part with 40 significant bits), e^r by its degree-13
+// Taylor polynomial in Horner order, scaled by 2^k.  tau above 50 returns 0
+// (no count below 2^63 keeps a transmitted photon there).
+__device__ __forceinline__ double exp_neg_spec(double tau) {
+  if (!(tau <= 50.0)) return 0.0;
+  const double x = -tau;
+  const double kf = rint(x * 0x1.71547652b82fep+0);
+  const double r = (x - kf * 0x1.62e42fefa2000p-1) - kf * 0x1.9ef35793c7673p-41;
+  double p = 0x1.6124613a86d09p-33;      // 1/13!
+  p = p * r + 0x1.1eed8eff8d898p-29;     // 1/12!
+  p = p * r + 0x1.ae64567f544e4p-26;     // 1/11!
+  p = p * r + 0x1.27e4fb7789f5cp-22;     // 1/10!
+  p = p * r + 0x1.71de3a556c734p-19;     // 1/9!
+  p = p * r + 0x1.a01a01a01a01ap-16;     // 1/8!
+  p = p * r + 0x1.a01a01a01a01ap-13;     // 1/7!
+  p = p * r + 0x1.6c16c16c16c17p-10;     // 1/6!
+  p = p * r + 0x1.1111111111111p-7;      // 1/5!
+  p = p * r + 0x1.5555555555555p-5;      // 1/4!
+  p = p * r + 0x1.5555555555555p-3;      // 1/3!
+  p = p * r + 0.5;
+  p = p * r + 1.0;
+  p = p * r + 1.0;
+  return ldexp(p, (int)kf);
+}
+
+// ceil(log2 x) for x > 0, exact
+__device__ __forceinline__ int ceil_log2_dev(double x) {
+  int e;
+  double m = frexp(x, &e);
+  return (m == 0.5) ? e - 1 : e;
+}
+
+// ---------------------------------------------------------------- lookups
+// index of the last box with key(box) <= v (boxes sorted by key)
+__device__ __forceinline__ int box_of_packet(const BoxMeta* b, int n, int64_t gid) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b[mid].pkt_off <= gid) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int box_of_cell(const BoxMeta* b, int n, int64_t cell) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b[mid].cell_off <= cell) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+}  // namespace crash

@@ -140,10 +140,15 @@ class Box:
     src_ndot: np.ndarray        # (n_src,) photons / s
     bin_eV: np.ndarray          # (n_bins,)
     bin_frac: np.ndarray        # (n_src, n_bins)
+    dims: Optional[tuple] = None  # (nx, ny, nz) for non-cubic grids; default (n, n, n)
 
     @property
     def n_src(self) -> int:
         return int(self.src_ndot.shape[0])
+
+    @property
+    def shape_xyz(self):
+        return tuple(self.dims) if self.dims is not None else (self.n, self.n, self.n)
 
 
 @dataclass

@@ -201,7 +201,7 @@ def test_axis_ray_attenuation_matches_eq1_by_hand():
     g.freeze()
     N0 = 123456789012345
     cr, N, esc, ab, (cells, segs) = g.trace([0.0, 1.5, 2.5], [1.0, 0.0, 0.0], [N0], log=10)
-    tau = nH * 6.30e-18 * dl
+    tau = float(np.float32(nH)) * 6.30e-18 * dl     # densities are float32 inputs
     expect = N0
     dep = g.read(oracle.F_DEP_HI).reshape(-1)
     for k, c in enumerate(cells):
