@@ -71,6 +71,9 @@ struct crash_ctx {
   void* wf = nullptr;
   int64_t launches = 0;          // kernels enqueued so far
   int64_t graph_launches = 0;    // kernels inside the captured step graph
+  int max_iter = 0;              // largest per-box DDA bound
+  int64_t n_keys = 0;            // wavefront re-sort keys over all boxes
+  int wf_mode = -1;              // wavefront option the workspace was sized for
 };
 
 static crash_status set_err(crash_ctx* c, crash_status st, const std::string& msg) {
@@ -221,12 +224,38 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
     m.T_cmb = d.z_compton >= 0 ? 2.725 * (1.0 + d.z_compton) : 0.0;
     m.seed = d.seed;
     m.caseB = d.caseB ? 1 : 0;
+    m.max_iter = d.nx + d.ny + d.nz + 3;
     off += m.ncell;
     c->any_he |= d.he_over_h > 0;
     c->any_heat |= !d.isothermal;
   }
   c->n_cells = off;
+  // wavefront sort keys: per box, Morton order of 8^3-cell buckets times 8 octants
+  int64_t keys = 0;
+  for (int i = 0; i < n_boxes; ++i) {
+    BoxMeta& m = c->meta[i];
+    int cmax = std::max(std::max((m.nx + 7) / 8, (m.ny + 7) / 8), (m.nz + 7) / 8);
+    int bits = 0;
+    while ((1 << bits) < cmax) ++bits;
+    m.bucket_bits = bits;
+    m.bucket_off = keys;
+    keys += (int64_t)8 << (3 * bits);
+    c->max_iter = std::max(c->max_iter, m.max_iter);
+  }
+  c->n_keys = keys;
   auto fail = [&](crash_status st) { release(c); return st; };
+  if (c->precision == CRASH_MIXED) {
+    for (int i = 0; i < n_boxes; ++i)
+      if (descs[i].nx > 65535 || descs[i].ny > 65535 || descs[i].nz > 65535 ||
+          (int64_t)descs[i].nx * descs[i].ny * descs[i].nz >= ((int64_t)1 << 31)) {
+        g_create_error = "mixed form: each axis <= 65535 cells and < 2^31 cells per box";
+        return fail(CRASH_ERR_OVERFLOW);
+      }
+    if (keys > (int64_t)4096 * 1024) {
+      g_create_error = "mixed form: too many boxes/cells for the re-sort key space";
+      return fail(CRASH_ERR_OVERFLOW);
+    }
+  }
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { g_create_error = cudaGetErrorString(e); return fail(CRASH_ERR_CUDA); }
   const size_t n = (size_t)c->n_cells;
@@ -460,7 +489,7 @@ static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, i
   launch_budget(a, c->tables, c->stream);
   *nk = 3 + (c->opts.chemistry ? 1 : 0);   // prep, budget, end-of-step, chemistry
   if (c->precision == CRASH_MIXED) {
-    int rc = launch_trace_mixed(a, c->tables, c->opts, c->wf, c->stream,
+    int rc = launch_trace_mixed(a, c->tables, c->opts, c->wf, c->max_iter, c->stream,
                                 timing ? &c->events : nullptr, &c->ev_used);
     if (rc < 0) return set_err(c, CRASH_ERR_CUDA, "mixed transport launch failed");
     *nk += rc;
@@ -519,10 +548,22 @@ extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t
   if (total > ((int64_t)1 << 40)) return set_err(c, CRASH_ERR_OVERFLOW, "too many packets in one step");
   CK(cudaMemcpyAsync(c->d_meta, c->meta.data(), sizeof(BoxMeta) * c->n_boxes,
                      cudaMemcpyHostToDevice, c->stream));
-  if (c->precision == CRASH_MIXED && !c->wf) {
-    int st = 0;
-    c->wf = wavefront_create(std::min<int64_t>(total, (int64_t)1 << 26), c->n_cells, c->n_bins, &st);
-    if (!c->wf) return set_err(c, CRASH_ERR_OOM, "wavefront workspace allocation failed");
+  if (c->precision == CRASH_MIXED) {
+    // packet queue: sized to the step (at most 2^26 packets per chunk); none
+    // when every packet is traced to the end by its own thread
+    const int64_t want = c->opts.wavefront ? std::min<int64_t>(total, (int64_t)1 << 26) : 0;
+    if (c->wf && (c->wf_mode != c->opts.wavefront || wavefront_capacity(c->wf) < want)) {
+      CK(cudaStreamSynchronize(c->stream));
+      wavefront_destroy(c->wf);
+      c->wf = nullptr;
+      if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    }
+    if (!c->wf) {
+      cudaError_t e = cudaSuccess;
+      c->wf = wavefront_create(want, c->n_keys, c->n_bins, &e);
+      if (!c->wf) return set_err(c, CRASH_ERR_OOM, std::string("wavefront workspace: ") + cudaGetErrorString(e));
+      c->wf_mode = c->opts.wavefront;
+    }
   }
   StepArgs a = make_args(c, dt, total);
   const bool timing = c->opts.timing != 0;

@@ -39,6 +39,11 @@ struct BoxMeta {
   uint32_t win_lo, win_hi; // traced packet ids [win_lo, win_hi) per source
   int64_t pkt_off;         // first global packet slot of this box in the launch
   int64_t pkt_count;       // n_src * (win_hi - win_lo)
+  // wavefront re-sort: keys of this box start at bucket_off; a key is
+  // morton(ix >> 3, iy >> 3, iz >> 3) (bucket_bits bits per axis) * 8 + octant
+  int64_t bucket_off;
+  int bucket_bits;
+  int max_iter;            // nx + ny + nz + 3: bound on DDA steps of one packet
 };
 
 // Cross sections and heating weights per species and bin (passed by value;
@@ -92,11 +97,15 @@ void launch_prep(const StepArgs& a, int precision, cudaStream_t s);
 void launch_budget(const StepArgs& a, const BinTables& t, cudaStream_t s);
 void launch_trace_fp64(const StepArgs& a, const BinTables& t, int block, cudaStream_t s);
 void launch_chemistry(const StepArgs& a, cudaStream_t s);
-int launch_trace_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o,
-                       void* wf_state, cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev,
-                       int* ev_used);
 
-// wavefront workspace (mixed form)
-void* wavefront_create(int64_t max_packets, int64_t n_cells_total, int n_bins, int* status);
+// Mixed-form transport.  Returns the number of kernels launched (>= 0) or
+// -1 on a launch error.  ev/ev_used: optional event pairs recorded around
+// the transport kernels.  max_iter: largest per-box DDA bound.
+typedef std::vector<std::pair<cudaEvent_t, cudaEvent_t>> EventPairs;
+int launch_trace_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o,
+                       void* wf_state, int max_iter, cudaStream_t s, EventPairs* ev, int* ev_used);
+
+// wavefront workspace (mixed form): capacity in packets, number of sort keys
+void* wavefront_create(int64_t capacity, int64_t n_keys, int n_bins, cudaError_t* err);
 void wavefront_destroy(void* w);
 int64_t wavefront_capacity(void* w);
