@@ -49,6 +49,10 @@ def workload(name):
         return inputs.stromgren_32(), native.CRASH_FP64_PLAIN
     if name == "lognormal_128":
         return inputs.lognormal_128(), native.CRASH_MIXED
+    if name == "lognormal_128_thin":
+        return inputs.lognormal_128(thin=True), native.CRASH_MIXED
+    if name == "lognormal_256_thin":      # profiling case: a few GB on the device
+        return inputs.lognormal_512(n=256, n_src=2000, packets=4_000_000, thin=True), native.CRASH_MIXED
     if name == "lognormal_512_thin":
         return inputs.lognormal_512(thin=True), native.CRASH_MIXED
     if name == "lognormal_512_neutral":
@@ -263,6 +267,9 @@ def run_crash(args):
     box = w.boxes[0]
     box.seed = box.seed + rank          # independent replica per rank
     P = w.packets_per_step[0]
+    if args.packets:
+        P = max(box.n_src, args.packets // box.n_src * box.n_src)
+        w.packets_per_step[0] = P
     g = native.Grid(box, prec)
     g.set_options(timing=1)
     stream = torch.cuda.ExternalStream(g.stream(), device=dev)
@@ -379,6 +386,8 @@ def run_crash(args):
             "gpu_launches": int(launches),
             "clocks": ck,
             "crossings_per_step": crossings / args.steps,
+            "transport_ms_per_step": kms / args.steps,
+            "chem_substeps_per_cell": float(tot1[7] - tot0[7]) / (args.steps * box.n ** 3),
         }
         print(json.dumps(line), flush=True)
     g.close()
@@ -396,6 +405,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--packets", type=int, default=0, help="override packets per step (small cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -48,6 +48,8 @@ struct crash_ctx {
   int* err = nullptr;
   int* boxE = nullptr;
   double *src_pos = nullptr, *src_ndot = nullptr, *src_frac = nullptr;
+  float* src_pos32 = nullptr;
+  int* src_cell = nullptr;
   int64_t *src_base = nullptr, *src_rem = nullptr;
   int n_src_total = 0, src_cap = 0;
   // bins
@@ -118,7 +120,7 @@ static void release(crash_ctx* c) {
   if (c->wf) wavefront_destroy(c->wf);
   void* ptrs[] = {c->nH, c->xHII, c->xHeII, c->xHeIII, c->T, c->abs64, c->abs32, c->dep,
                   c->d_meta, c->budget, c->totals, c->step_dev, c->err, c->boxE, c->src_pos, c->src_ndot,
-                  c->src_frac, c->src_base, c->src_rem};
+                  c->src_frac, c->src_base, c->src_rem, c->src_pos32, c->src_cell};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -220,6 +222,7 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
     m.cell_off = off;
     m.ncell = (int64_t)d.nx * d.ny * d.nz;
     m.dl = d.box_cm / d.nx;
+    m.dlf = (float)m.dl;
     m.he = d.he_over_h;
     m.T_cmb = d.z_compton >= 0 ? 2.725 * (1.0 + d.z_compton) : 0.0;
     m.seed = d.seed;
@@ -339,11 +342,16 @@ static crash_status rebuild_sources(crash_ctx* c) {
   }
   const int nb = c->n_bins;
   if (total > c->src_cap) {
-    void* old[] = {c->src_pos, c->src_ndot, c->src_frac, c->src_base, c->src_rem};
+    void* old[] = {c->src_pos, c->src_ndot, c->src_frac, c->src_base, c->src_rem, c->src_pos32,
+                   c->src_cell};
     for (void* p : old)
       if (p) cudaFree(p);
     c->src_pos = c->src_ndot = c->src_frac = nullptr;
     c->src_base = c->src_rem = nullptr;
+    c->src_pos32 = nullptr;
+    c->src_cell = nullptr;
+    CK(cudaMalloc(&c->src_pos32, sizeof(float) * 3 * total));
+    CK(cudaMalloc(&c->src_cell, sizeof(int) * 3 * total));
     CK(cudaMalloc(&c->src_pos, sizeof(double) * 3 * total));
     CK(cudaMalloc(&c->src_ndot, sizeof(double) * total));
     CK(cudaMalloc(&c->src_frac, sizeof(double) * total * CRASH_MAX_BINS));
@@ -361,6 +369,14 @@ static crash_status rebuild_sources(crash_ctx* c) {
   }
   c->n_src_total = total;
   if (total) {
+    std::vector<float> pos32(pos.size());
+    std::vector<int> cell(pos.size());
+    for (size_t i = 0; i < pos.size(); ++i) {
+      pos32[i] = (float)pos[i];
+      cell[i] = (int)floor(pos[i]);
+    }
+    CK(cudaMemcpy(c->src_pos32, pos32.data(), pos32.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->src_cell, cell.data(), cell.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->src_pos, pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->src_ndot, ndot.data(), ndot.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->src_frac, frac.data(), frac.size() * 8, cudaMemcpyHostToDevice));
@@ -466,6 +482,7 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
   a.dt = dt;
   a.total_packets = total;
   a.src_pos = c->src_pos; a.src_ndot = c->src_ndot; a.src_frac = c->src_frac;
+  a.src_pos32 = c->src_pos32; a.src_cell = c->src_cell;
   a.src_base = c->src_base; a.src_rem = c->src_rem;
   a.box_E = c->boxE;
   a.n_src_total = c->n_src_total;
@@ -476,6 +493,7 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
   a.err = c->err;
   a.any_he = c->any_he; a.any_heat = c->any_heat;
   a.chemistry = c->opts.chemistry;
+  a.fp32_rates = c->precision == CRASH_MIXED;
   a.chem_eps = c->opts.chem_eps;
   a.chem_max_sub = c->opts.chem_max_sub;
   a.cool_mask = c->opts.cool_mask;
@@ -731,12 +749,24 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   crash_run_opts base = c->opts;
   crash_run_opts best = base;
   double best_ms = 1e300;
+  // trials trace a window of about 2^24 packets (one wavefront chunk or less)
+  uint32_t win = 0xFFFFFFFFu;
+  {
+    int64_t tot = 0;
+    for (int b = 0; b < c->n_boxes; ++b) tot += (int64_t)P[b];
+    if (tot > ((int64_t)1 << 24)) {
+      uint64_t mx = 1;
+      for (int b = 0; b < c->n_boxes; ++b) mx = std::max<uint64_t>(mx, P[b] / (uint64_t)c->meta[b].n_src);
+      win = (uint32_t)std::max<uint64_t>(1, (uint64_t)((double)mx * (double)((int64_t)1 << 24) / (double)tot));
+    }
+  }
   std::vector<int> blocks = {64, 128, 256};
   std::vector<int> segs = {0};
   std::vector<int> resorts = {0};
   if (c->precision == CRASH_MIXED) {
-    segs = {16, 32, 64, 128};
-    resorts = {-1, 1, 2, 4};
+    blocks = {128, 256};
+    segs = {16, 32, 64};
+    resorts = {-1, 1, 2};
   }
   crash_status st = CRASH_OK;
   for (int bs : blocks)
@@ -746,6 +776,8 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
         o.block_size = bs;
         o.seg_per_iter = sg;
         o.resort_interval = rs;
+        o.pkt_begin = 0;
+        o.pkt_end = win;
         o.chemistry = 0;
         o.use_graph = 0;
         o.timing = 0;

@@ -26,6 +26,7 @@ struct BoxMeta {
   int64_t cell_off;    // first cell of the box in the concatenated arrays
   int64_t ncell;
   double dl;           // cell edge, cm
+  float dlf;           // the same in FP32 (mixed form)
   double he;           // n_He / n_H
   double T_cmb;        // 0 => Compton off
   uint64_t seed;
@@ -64,6 +65,8 @@ struct StepArgs {
   int64_t total_packets;
   // sources
   const double* src_pos;     // [n_src_total][3]
+  const float* src_pos32;    // [n_src_total][3] the same in FP32 (mixed form)
+  const int* src_cell;       // [n_src_total][3] cell of each source
   const double* src_ndot;    // [n_src_total]
   const double* src_frac;    // [n_src_total][n_bins]
   int64_t* src_base;         // [n_src_total][n_bins]  per-packet content base (written per step)
@@ -84,6 +87,7 @@ struct StepArgs {
   int any_he;                // some box has helium (selects the H+He kernels)
   int any_heat;              // some box evolves T (selects the heating deposit)
   int chemistry;
+  int fp32_rates;            // mixed form: rate fits evaluated in FP32
   double chem_eps;
   int chem_max_sub;
   int cool_mask;

@@ -52,40 +52,46 @@ struct Rates {
 // Hui & Gnedin (1997) recombination (case A/B) and recombination cooling;
 // Cen (1992) collisional ionisation, collisional excitation cooling and
 // dielectronic recombination; bremsstrahlung 1.42e-27 g_ff sqrt(T).
-__device__ Rates rates_at(double T, int caseB) {
+// R = double in the FP64 form; R = float in the mixed form, where the fits
+// (themselves accurate to a few per cent) are evaluated in FP32 and the
+// integration stays in FP64.
+template <typename R>
+__device__ Rates rates_at(double Td, int caseB) {
   Rates r;
-  const double lH = 315614.0 / T, lHe1 = 570670.0 / T, lHe2 = 1263030.0 / T;
-  const double sq = 1.0 / (1.0 + sqrt(T / 1e5));
+  const R T = (R)Td;
+  const R one = (R)1, lH = (R)315614.0 / T, lHe1 = (R)570670.0 / T, lHe2 = (R)1263030.0 / T;
+  const R sq = one / (one + sqrt(T / (R)1e5));
   if (caseB) {
-    r.aHII = 2.753e-14 * pow(lH, 1.5) / pow(1.0 + pow(lH / 2.740, 0.407), 2.242);
-    r.aHeII = 1.26e-14 * pow(lHe1, 0.750);
-    r.aHeIII = 2.0 * 2.753e-14 * pow(lHe2, 1.5) / pow(1.0 + pow(lHe2 / 2.740, 0.407), 2.242);
-    r.crecHII = 3.435e-30 * T * pow(lH, 1.970) / pow(1.0 + pow(lH / 2.250, 0.376), 3.720);
-    r.crecHeIII = 8.0 * 3.435e-30 * (0.25 * T) * pow(lHe2, 1.970) /
-                  pow(1.0 + pow(lHe2 / 2.250, 0.376), 3.720);
+    r.aHII = (R)2.753e-14 * pow(lH, (R)1.5) / pow(one + pow(lH / (R)2.740, (R)0.407), (R)2.242);
+    r.aHeII = (R)1.26e-14 * pow(lHe1, (R)0.750);
+    r.aHeIII = (R)2 * (R)2.753e-14 * pow(lHe2, (R)1.5) / pow(one + pow(lHe2 / (R)2.740, (R)0.407), (R)2.242);
+    r.crecHII = (double)((R)3.435e-30 * T * pow(lH, (R)1.970) / pow(one + pow(lH / (R)2.250, (R)0.376), (R)3.720));
+    r.crecHeIII = (double)((R)8 * (R)3.435e-30 * ((R)0.25 * T) * pow(lHe2, (R)1.970) /
+                           pow(one + pow(lHe2 / (R)2.250, (R)0.376), (R)3.720));
   } else {
-    r.aHII = 1.269e-13 * pow(lH, 1.503) / pow(1.0 + pow(lH / 0.522, 0.470), 1.923);
-    r.aHeII = 3.0e-14 * pow(lHe1, 0.654);
-    r.aHeIII = 2.0 * 1.269e-13 * pow(lHe2, 1.503) / pow(1.0 + pow(lHe2 / 0.522, 0.470), 1.923);
-    r.crecHII = 1.778e-29 * T * pow(lH, 1.965) / pow(1.0 + pow(lH / 0.541, 0.502), 2.697);
-    r.crecHeIII = 8.0 * 1.778e-29 * (0.25 * T) * pow(lHe2, 1.965) /
-                  pow(1.0 + pow(lHe2 / 0.541, 0.502), 2.697);
+    r.aHII = (R)1.269e-13 * pow(lH, (R)1.503) / pow(one + pow(lH / (R)0.522, (R)0.470), (R)1.923);
+    r.aHeII = (R)3.0e-14 * pow(lHe1, (R)0.654);
+    r.aHeIII = (R)2 * (R)1.269e-13 * pow(lHe2, (R)1.503) / pow(one + pow(lHe2 / (R)0.522, (R)0.470), (R)1.923);
+    r.crecHII = (double)((R)1.778e-29 * T * pow(lH, (R)1.965) / pow(one + pow(lH / (R)0.541, (R)0.502), (R)2.697));
+    r.crecHeIII = (double)((R)8 * (R)1.778e-29 * ((R)0.25 * T) * pow(lHe2, (R)1.965) /
+                           pow(one + pow(lHe2 / (R)0.541, (R)0.502), (R)2.697));
   }
-  r.adiel = 1.90e-3 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T));
-  const double rt = sqrt(T);
-  r.bHI = 5.85e-11 * rt * exp(-157809.1 / T) * sq;
-  r.bHeI = 2.38e-11 * rt * exp(-285335.4 / T) * sq;
-  r.bHeII = 5.68e-12 * rt * exp(-631515.0 / T) * sq;
-  const double lg = log10(T);
-  const double gff = 1.1 + 0.34 * exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
-  r.cexHI = 7.50e-19 * exp(-118348.0 / T) * sq;
-  r.cexHeII = 5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) * sq;
+  r.adiel = (double)((R)1.90e-3 * pow(T, (R)-1.5) * exp((R)-470000.0 / T) * (one + (R)0.3 * exp((R)-94000.0 / T)));
+  const R rt = sqrt(T);
+  const R bHI = (R)5.85e-11 * rt * exp((R)-157809.1 / T) * sq;
+  const R bHeI = (R)2.38e-11 * rt * exp((R)-285335.4 / T) * sq;
+  const R bHeII = (R)5.68e-12 * rt * exp((R)-631515.0 / T) * sq;
+  r.bHI = bHI; r.bHeI = bHeI; r.bHeII = bHeII;
+  const R lg = log10(T);
+  const R gff = (R)1.1 + (R)0.34 * exp(-((R)5.5 - lg) * ((R)5.5 - lg) / (R)3.0);
+  r.cexHI = (double)((R)7.50e-19 * exp((R)-118348.0 / T) * sq);
+  r.cexHeII = (double)((R)5.54e-17 * pow(T, (R)-0.397) * exp((R)-473638.0 / T) * sq);
   r.cionHI = 13.6 * eV * r.bHI;
   r.cionHeI = 24.6 * eV * r.bHeI;
   r.cionHeII = 54.4 * eV * r.bHeII;
-  r.crecHeII = kB * T * r.aHeII;
+  r.crecHeII = kB * Td * r.aHeII;
   r.cdiel = 6.526e-11 * r.adiel;
-  r.cff = 1.42e-27 * gff * rt;
+  r.cff = (double)((R)1.42e-27 * gff * rt);
   return r;
 }
 
@@ -107,6 +113,7 @@ struct CellIn {
 };
 
 // returns sub-steps; updates x (HII), y2 (HeII), y3 (HeIII), T
+template <typename RT>
 __device__ int integrate_cell(const CellIn& c, double dt, double& x, double& y2, double& y3,
                               double& T) {
   const bool coll = (c.mask & 2) != 0, rec = (c.mask & 4) != 0, diel = (c.mask & 32) != 0;
@@ -114,7 +121,7 @@ __device__ int integrate_cell(const CellIn& c, double dt, double& x, double& y2,
   double rem = dt;
   int nsub = 0;
   while (rem > 0.0) {
-    const Rates r = rates_at(T, c.caseB);
+    const Rates r = rates_at<RT>(T, c.caseB);
     const double aH = rec ? r.aHII : 0.0;
     const double aHe2 = rec ? r.aHeII + (diel ? r.adiel : 0.0) : 0.0;
     const double aHe3 = rec ? r.aHeIII : 0.0;
@@ -206,6 +213,7 @@ __device__ int integrate_cell(const CellIn& c, double dt, double& x, double& y2,
 
 }  // namespace
 
+template <typename RT>
 __global__ void __launch_bounds__(128) k_chemistry(StepArgs a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long subs = 0;
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(128) k_chemistry(StepArgs a) {
     }
     c.eps = a.chem_eps;
     c.max_sub = a.chem_max_sub;
-    subs = (unsigned long long)integrate_cell(c, a.dt, x, y2, y3, T);
+    subs = (unsigned long long)integrate_cell<RT>(c, a.dt, x, y2, y3, T);
     a.xHII[i] = x;
     a.xHeII[i] = y2;
     a.xHeIII[i] = y3;
@@ -265,5 +273,6 @@ __global__ void __launch_bounds__(128) k_chemistry(StepArgs a) {
 void launch_chemistry(const StepArgs& a, cudaStream_t s) {
   if (a.n_cells_total <= 0) return;
   int64_t blocks = (a.n_cells_total + 127) / 128;
-  k_chemistry<<<(unsigned)blocks, 128, 0, s>>>(a);
+  if (a.fp32_rates) k_chemistry<float><<<(unsigned)blocks, 128, 0, s>>>(a);
+  else k_chemistry<double><<<(unsigned)blocks, 128, 0, s>>>(a);
 }

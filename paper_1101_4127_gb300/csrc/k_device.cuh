@@ -64,6 +64,27 @@ __device__ __forceinline__ bool iso_direction(uint64_t seed, uint32_t step, uint
   return false;
 }
 
+// The same draws with the acceptance test in FP64 (so that every packet
+// takes the same attempt as in the FP64 form) and the direction in FP32.
+__device__ __forceinline__ bool iso_direction_f32(uint64_t seed, uint32_t step, uint32_t src,
+                                                  uint32_t pkt, float& dx, float& dy, float& dz) {
+  for (uint32_t a = 0; a < 64u; ++a) {
+    uint4 r = philox10(make_uint4(pkt, src, step, a), seed);
+    double v1 = 2.0 * uniform53(r.x, r.y) - 1.0;
+    double v2 = 2.0 * uniform53(r.z, r.w) - 1.0;
+    double s = v1 * v1 + v2 * v2;
+    if (s < 1.0 && s != 0.0) {
+      const float sf = (float)s;
+      const float root = sqrtf(1.0f - sf);
+      dx = (2.0f * (float)v1) * root;
+      dy = (2.0f * (float)v2) * root;
+      dz = 1.0f - 2.0f * sf;
+      return true;
+    }
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------- exp(-tau)
 // e^-tau, tau >= 0: split -tau = k ln2 + r (Cody & Waite 1980 two-constant
 // reduction, ln2 high part with 40 significant bits), e^r by its degree-13

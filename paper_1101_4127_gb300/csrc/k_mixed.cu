@@ -4,9 +4,8 @@
 // the FP64 form).
 //
 // Per crossed cell and bin j (Sec. 2, Eq. 1): tau_j = l sum_s n_s sigma_s,j;
-// the absorbed count A_j = rint(N_j (1 - e^-tau_j)) is formed in integer
-// arithmetic from a 0.32 fixed-point absorption fraction, so N' = N - A
-// keeps the photon budget exact; the species split (Sec. 2) and the
+// the absorbed count A_j = rint(N_j (1 - e^-tau_j)) <= N_j is an integer and
+// N' = N - A, so the photon budget stays exact; the species split (Sec. 2) and the
 // heating energy are accumulated in FP32 over the bins and rounded once per
 // cell, H I taking the remainder.
 //
@@ -31,16 +30,21 @@ using namespace crash;
 
 namespace {
 
+// Packet records (array of structures, one per packet, RS bytes):
+//   [0,16)  float4 (tMx, tMy, tMz, dx)   distances to the next faces, x direction
+//   [16,24) uint2  (ix | iy << 16, iz | box << 16)
+//   [24,32) float2 (dy, dz)
+//   [32, )  int64  N[n_bins]             photon content per bin
+// RS = 32 + 8 n_bins rounded up to 16 bytes (96 for 8 bins).
 struct WF {
   int64_t cap = 0;
   int nb = 0;
-  uint2* cb[2] = {nullptr, nullptr};     // (ix | iy << 16, iz | box << 16)
-  float4* td[2] = {nullptr, nullptr};    // (tMx, tMy, tMz, dx): distances to the next faces
-  float2* dyz[2] = {nullptr, nullptr};   // (dy, dz)
-  long long* N[2] = {nullptr, nullptr};  // [bin][cap] packet contents
+  int rs = 0;                            // record size in bytes
+  char* rec[2] = {nullptr, nullptr};
   unsigned* count = nullptr;             // [4]: live counts of buffers 0 and 1
-  unsigned* key = nullptr;               // [cap] sort key per packet
-  unsigned* rank = nullptr;              // [cap] rank inside its key
+  unsigned* key = nullptr;               // [cap] sort key of each written record
+  unsigned* rank = nullptr;              // [cap] its rank among equal keys
+  unsigned* perm = nullptr;              // [cap] sorted position -> record index
   unsigned* bcount = nullptr;            // [n_keys]
   unsigned* boff = nullptr;              // [n_keys]
   unsigned* bsum = nullptr;              // [1024]
@@ -48,10 +52,15 @@ struct WF {
 };
 
 struct WFArgs {
-  uint2* cb_in; float4* td_in; float2* dyz_in; long long* N_in;
-  uint2* cb_out; float4* td_out; float2* dyz_out; long long* N_out;
+  const char* rec_in;
+  char* rec_out;
   const unsigned* count_in;
   unsigned* count_out;
+  const unsigned* perm;      // non-null: read record perm[j] at position j
+  unsigned* key;             // non-null: record the sort key and rank of every survivor
+  unsigned* rank;
+  unsigned* bcount;
+  int rs;
   int64_t cap;
 };
 
@@ -87,20 +96,58 @@ __device__ __forceinline__ void flush_warp(const StepArgs& a, int b, Tally& t) {
   t = Tally{0, 0, 0, 0, 0};
 }
 
-// round(N * G / 2^32) for a 0.32 fixed-point fraction G < 2^32 (result <= N)
-__device__ __forceinline__ long long mul_frac(long long N, unsigned G) {
-  const unsigned long long n = (unsigned long long)N;
-  const unsigned long long lo = (n & 0xFFFFFFFFull) * (unsigned long long)G;
-  const unsigned long long hi = (n >> 32) * (unsigned long long)G;
-  return (long long)(hi + ((lo + 0x80000000ull) >> 32));
+// int64 <-> FP32 conversions done with integer ALU operations: on this GPU
+// the hardware 64-bit conversions issue to the FP64 pipe, which is narrow.
+// N in [0, 2^63) to FP32 by truncation to 24 significant bits (relative
+// error below 2^-23).
+__device__ __forceinline__ float ll_to_float(long long N) {
+  const unsigned long long u = (unsigned long long)N;
+  if (u == 0ull) return 0.0f;
+  const int lz = __clzll(u);
+  const unsigned long long norm = u << lz;
+  const unsigned mant = (unsigned)(norm >> 40) & 0x7FFFFFu;
+  return __uint_as_float(((unsigned)(190 - lz) << 23) | mant);
 }
 
-// 1 - exp(-tau) in FP32 with small relative error for small tau
-__device__ __forceinline__ float absorbed_fraction(float tau) {
-  if (tau < 0.05f) {
-    return tau * (1.0f - 0.5f * tau * (1.0f - (1.0f / 3.0f) * tau * (1.0f - 0.25f * tau)));
+// rint(x) for x in [0, 2^63), round half to even
+__device__ __forceinline__ long long float_to_ll(float x) {
+  if (x < 8388608.0f)   // below 2^23 adding 2^23 rounds to an integer in the last place
+    return (long long)(__float_as_uint(x + 8388608.0f) - 0x4B000000u);
+  const unsigned b = __float_as_uint(x);
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  return (long long)(m << ((int)(b >> 23) - 150));
+}
+
+// 1 - exp(-tau) for 0 < tau < 0.5 by its Taylor series to tau^8
+// (truncation below 2e-8 relative)
+__device__ __forceinline__ float absorbed_fraction_small(float tau) {
+  float p = -1.0f / 40320.0f;
+  p = fmaf(p, tau, 1.0f / 5040.0f);
+  p = fmaf(p, tau, -1.0f / 720.0f);
+  p = fmaf(p, tau, 1.0f / 120.0f);
+  p = fmaf(p, tau, -1.0f / 24.0f);
+  p = fmaf(p, tau, 1.0f / 6.0f);
+  p = fmaf(p, tau, -0.5f);
+  p = fmaf(p, tau, 1.0f);
+  return tau * p;
+}
+
+// Absorbed count of one bin: for tau < 0.5 round N (1 - e^-tau), else round
+// the transmitted N e^-tau and take the difference, so that the smaller of
+// the two parts always carries ~1e-7 relative error.  Af is the absorbed
+// count in FP32 (for the species and heating weights).
+__device__ __forceinline__ long long absorb(long long N, float tau, float& Af) {
+  const float Nf = ll_to_float(N);
+  if (tau < 0.5f) {
+    Af = Nf * absorbed_fraction_small(tau);
+    const long long A = float_to_ll(Af);
+    return A > N ? N : A;
   }
-  return 1.0f - __expf(-tau);
+  const float T = Nf * expf(-tau);
+  Af = Nf - T;
+  long long Np = float_to_ll(T);
+  Np = Np > N ? N : Np;
+  return N - Np;
 }
 
 enum { ALIVE = 0, ABSORBED = 1, ESCAPED = 2 };
@@ -119,7 +166,7 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
   const float tDy = dy != 0.f ? 1.0f / fabsf(dy) : INFINITY;
   const float tDz = dz != 0.f ? 1.0f / fabsf(dz) : INFINITY;
   const int sx = dx > 0.f ? 1 : -1, sy = dy > 0.f ? 1 : -1, sz = dz > 0.f ? 1 : -1;
-  const float dl = (float)M->dl;
+  const float dl = M->dlf;
   const int64_t coff = M->cell_off;
   const bool heat_box = HEAT && !M->isothermal;
   const float4* __restrict__ abs32 = reinterpret_cast<const float4*>(a.abs32);
@@ -146,13 +193,12 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
         }
         long long Nj = N[j];
         if (tau > 0.f && Nj > 0) {
-          const float g = absorbed_fraction(tau);
-          const long long A = g >= 1.0f ? Nj : mul_frac(Nj, (unsigned)(g * 4294967296.0f));
+          float Af;
+          const long long A = absorb(Nj, tau, Af);
           Nj -= A;
           N[j] = Nj;
           Atot += A;
           if (HE || HEAT) {
-            const float Af = (float)A;
             const float inv = __frcp_rn(tau);
             if (HE) {
               fHeI += Af * (k1 * inv);
@@ -171,9 +217,9 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
       if (Atot) {
         long long dHeI = 0, dHeII = 0;
         if (HE) {
-          dHeI = __float2ll_rn(fHeI);
+          dHeI = float_to_ll(fHeI);
           dHeI = dHeI > Atot ? Atot : dHeI;
-          dHeII = __float2ll_rn(fHeII);
+          dHeII = float_to_ll(fHeII);
           dHeII = dHeII > Atot - dHeI ? Atot - dHeI : dHeII;
         }
         const long long dHI = Atot - dHeI - dHeII;
@@ -182,7 +228,7 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
         if (dHeI) atomicAdd(dp + 1, (unsigned long long)dHeI);
         if (dHeII) atomicAdd(dp + 2, (unsigned long long)dHeII);
         if (heat_box) {
-          const long long h = __float2ll_rn(fheat);
+          const long long h = float_to_ll(fheat);
           if (h) atomicAdd(dp + 3, (unsigned long long)h);
         }
         tl.absorbed += (unsigned long long)Atot;
@@ -221,24 +267,95 @@ __device__ __forceinline__ long long append_slot(bool alive, unsigned* count_out
   return (long long)base + __popc(m & ((1u << lane) - 1u));
 }
 
+__device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every third bit
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// sort key: Morton order of the packet's 8^3-cell bucket, then direction octant
+__device__ __forceinline__ unsigned sort_key(const BoxMeta* boxes, int box, int ix, int iy, int iz,
+                                             float dx, float dy, float dz) {
+  const unsigned oct = (dx < 0.f ? 1u : 0u) | (dy < 0.f ? 2u : 0u) | (dz < 0.f ? 4u : 0u);
+  const unsigned mort = spread3((unsigned)ix >> 3) | (spread3((unsigned)iy >> 3) << 1) |
+                        (spread3((unsigned)iz >> 3) << 2);
+  return (unsigned)boxes[box].bucket_off + ((mort << 3) | oct);
+}
+
 template <int NBT>
-__device__ __forceinline__ void store_packet(const WFArgs& w, long long slot, int ix, int iy, int iz,
+__device__ __forceinline__ void store_record(char* rec, int rs, long long slot, int ix, int iy, int iz,
                                              int box, float tMx, float tMy, float tMz, float dx,
                                              float dy, float dz, const long long* N, int nb) {
-  w.cb_out[slot] = make_uint2((unsigned)ix | ((unsigned)iy << 16), (unsigned)iz | ((unsigned)box << 16));
-  w.td_out[slot] = make_float4(tMx, tMy, tMz, dx);
-  w.dyz_out[slot] = make_float2(dy, dz);
+  char* r = rec + (int64_t)rs * slot;
+  *reinterpret_cast<float4*>(r) = make_float4(tMx, tMy, tMz, dx);
+  *reinterpret_cast<uint4*>(r + 16) =
+      make_uint4((unsigned)ix | ((unsigned)iy << 16), (unsigned)iz | ((unsigned)box << 16),
+                 __float_as_uint(dy), __float_as_uint(dz));
+  longlong2* n2 = reinterpret_cast<longlong2*>(r + 32);
 #pragma unroll
-  for (int j = 0; j < (NBT > 0 ? NBT : CRASH_MAX_BINS); ++j) {
-    if (NBT == 0 && j >= nb) break;
-    w.N_out[(int64_t)j * w.cap + slot] = N[j];
+  for (int j = 0; j < (NBT > 0 ? (NBT + 1) / 2 : CRASH_MAX_BINS / 2); ++j) {
+    if (NBT == 0 && 2 * j >= nb) break;
+    n2[j] = make_longlong2(N[2 * j], (2 * j + 1 < nb) ? N[2 * j + 1] : 0ll);
+  }
+}
+
+template <int NBT>
+__device__ __forceinline__ void load_record(const char* rec, int rs, long long i, int& ix, int& iy,
+                                            int& iz, int& box, float& tMx, float& tMy, float& tMz,
+                                            float& dx, float& dy, float& dz, long long* N, int nb) {
+  const char* r = rec + (int64_t)rs * i;
+  const float4 td = *reinterpret_cast<const float4*>(r);
+  const uint4 cd = *reinterpret_cast<const uint4*>(r + 16);
+  tMx = td.x; tMy = td.y; tMz = td.z; dx = td.w;
+  ix = (int)(cd.x & 0xFFFFu); iy = (int)(cd.x >> 16);
+  iz = (int)(cd.y & 0xFFFFu); box = (int)(cd.y >> 16);
+  dy = __uint_as_float(cd.z); dz = __uint_as_float(cd.w);
+  const longlong2* n2 = reinterpret_cast<const longlong2*>(r + 32);
+#pragma unroll
+  for (int j = 0; j < (NBT > 0 ? (NBT + 1) / 2 : CRASH_MAX_BINS / 2); ++j) {
+    if (NBT == 0 && 2 * j >= nb) break;
+    const longlong2 v = n2[j];
+    N[2 * j] = v.x;
+    if (2 * j + 1 < (NBT > 0 ? NBT : CRASH_MAX_BINS)) N[2 * j + 1] = v.y;
+  }
+}
+
+// Write the survivors of a warp: append slot, record, and (when the next
+// pass reads in sorted order) the record's key and its rank among the
+// records of that key (one atomic per group of equal keys in the warp).
+template <int NBT>
+__device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& w, bool alive, int ix,
+                                               int iy, int iz, int box, float tMx, float tMy, float tMz,
+                                               float dx, float dy, float dz, const long long* N, int nb) {
+  const long long slot = append_slot(alive, w.count_out);
+  bool ok = alive;
+  if (alive && slot >= w.cap) {
+    atomicOr(a.err, ERR_QUEUE);
+    ok = false;
+  }
+  if (ok) store_record<NBT>(w.rec_out, w.rs, slot, ix, iy, iz, box, tMx, tMy, tMz, dx, dy, dz, N, nb);
+  if (w.key) {
+    const unsigned k = ok ? sort_key(a.boxes, box, ix, iy, iz, dx, dy, dz) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+    if (ok) {
+      const int lane = threadIdx.x & 31;
+      const int leader = __ffs(peers) - 1;
+      unsigned r0 = 0;
+      if (lane == leader) r0 = atomicAdd(&w.bcount[k], (unsigned)__popc(peers));
+      r0 = __shfl_sync(peers, r0, leader);
+      w.key[slot] = k;
+      w.rank[slot] = r0 + __popc(peers & ((1u << lane) - 1u));
+    }
   }
 }
 
 // ------------------------------------------------------------------ emission
 template <int NBT, bool HE, bool HEAT>
 __global__ void __launch_bounds__(256) k_emit_mixed(StepArgs a, BinTables t, WFArgs w, int64_t g0,
-                                                   int64_t n, int S) {
+                                                   int64_t n, int S, int max_steps_all) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const uint32_t step = (uint32_t)*a.step_dev;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -259,8 +376,7 @@ __global__ void __launch_bounds__(256) k_emit_mixed(StepArgs a, BinTables t, WFA
       const int s_local = (int)(local / W);
       const uint32_t p = M->win_lo + (uint32_t)(local - (int64_t)s_local * W);
       const int s = M->src_off + s_local;
-      double dx, dy, dz;
-      if (!iso_direction(M->seed, step, (uint32_t)s_local, p, dx, dy, dz)) {
+      if (!iso_direction_f32(M->seed, step, (uint32_t)s_local, p, fx, fy, fz)) {
         atomicOr(a.err, ERR_DIRECTION);
       } else {
         for (int j = 0; j < nb; ++j) {
@@ -270,13 +386,12 @@ __global__ void __launch_bounds__(256) k_emit_mixed(StepArgs a, BinTables t, WFA
           tl.emitted += (unsigned long long)N[j];
         }
         tl.packets += 1;
-        const double px = a.src_pos[3 * s], py = a.src_pos[3 * s + 1], pz = a.src_pos[3 * s + 2];
-        ix = (int)floor(px); iy = (int)floor(py); iz = (int)floor(pz);
-        // distances to the first faces, formed in FP64 then rounded once
-        tMx = dx > 0 ? (float)(((double)(ix + 1) - px) / dx) : (dx < 0 ? (float)(((double)ix - px) / dx) : INFINITY);
-        tMy = dy > 0 ? (float)(((double)(iy + 1) - py) / dy) : (dy < 0 ? (float)(((double)iy - py) / dy) : INFINITY);
-        tMz = dz > 0 ? (float)(((double)(iz + 1) - pz) / dz) : (dz < 0 ? (float)(((double)iz - pz) / dz) : INFINITY);
-        fx = (float)dx; fy = (float)dy; fz = (float)dz;
+        const float px = a.src_pos32[3 * s], py = a.src_pos32[3 * s + 1], pz = a.src_pos32[3 * s + 2];
+        ix = a.src_cell[3 * s]; iy = a.src_cell[3 * s + 1]; iz = a.src_cell[3 * s + 2];
+        // distances along the ray to the first x/y/z faces
+        tMx = fx > 0.f ? ((float)(ix + 1) - px) / fx : (fx < 0.f ? ((float)ix - px) / fx : INFINITY);
+        tMy = fy > 0.f ? ((float)(iy + 1) - py) / fy : (fy < 0.f ? ((float)iy - py) / fy : INFINITY);
+        tMz = fz > 0.f ? ((float)(iz + 1) - pz) / fz : (fz < 0.f ? ((float)iz - pz) / fz : INFINITY);
         const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
                                                  nb, S, tl);
         if (r == ESCAPED) {
@@ -285,11 +400,8 @@ __global__ void __launch_bounds__(256) k_emit_mixed(StepArgs a, BinTables t, WFA
         alive = (r == ALIVE);
       }
     }
-    const long long slot = append_slot(alive, w.count_out);
-    if (alive) {
-      if (slot >= w.cap) atomicOr(a.err, ERR_QUEUE);
-      else store_packet<NBT>(w, slot, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
-    }
+    if (S < max_steps_all)   // a wavefront launch: keep the survivors
+      write_survivor<NBT>(a, w, alive, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
     flush_warp(a, b, tl);
   }
 }
@@ -302,81 +414,29 @@ __global__ void __launch_bounds__(256) k_pass_mixed(StepArgs a, BinTables t, WFA
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   Tally tl{0, 0, 0, 0, 0};
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t i = base + threadIdx.x;
+    const int64_t j = base + threadIdx.x;
     int b = -1;
     bool alive = false;
     int ix = 0, iy = 0, iz = 0;
     float tMx = 0.f, tMy = 0.f, tMz = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     long long N[NBT > 0 ? NBT : CRASH_MAX_BINS];
-    if (i < n) {
-      const uint2 cb = w.cb_in[i];
-      const float4 td = w.td_in[i];
-      const float2 dd = w.dyz_in[i];
-      ix = (int)(cb.x & 0xFFFFu); iy = (int)(cb.x >> 16);
-      iz = (int)(cb.y & 0xFFFFu); b = (int)(cb.y >> 16);
-      tMx = td.x; tMy = td.y; tMz = td.z; fx = td.w; fy = dd.x; fz = dd.y;
-#pragma unroll
-      for (int j = 0; j < (NBT > 0 ? NBT : CRASH_MAX_BINS); ++j) {
-        if (NBT == 0 && j >= nb) break;
-        N[j] = w.N_in[(int64_t)j * w.cap + i];
-      }
+    if (j < n) {
+      const int64_t i = w.perm ? (int64_t)w.perm[j] : j;
+      load_record<NBT>(w.rec_in, w.rs, i, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
       const BoxMeta* M = a.boxes + b;
       const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
                                                nb, S, tl);
       if (r == ESCAPED) {
-        for (int j = 0; j < nb; ++j) tl.escaped += (unsigned long long)N[j];
+        for (int jj = 0; jj < nb; ++jj) tl.escaped += (unsigned long long)N[jj];
       }
       alive = (r == ALIVE);
     }
-    const long long slot = append_slot(alive, w.count_out);
-    if (alive) {
-      if (slot >= w.cap) atomicOr(a.err, ERR_QUEUE);
-      else store_packet<NBT>(w, slot, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
-    }
+    write_survivor<NBT>(a, w, alive, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
     flush_warp(a, b, tl);
   }
 }
 
 // ------------------------------------------------------------------ re-sort
-__device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every third bit
-  v &= 0x3FFu;
-  v = (v | (v << 16)) & 0x030000FFu;
-  v = (v | (v << 8)) & 0x0300F00Fu;
-  v = (v | (v << 4)) & 0x030C30C3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
-__global__ void k_sort_keys(StepArgs a, WFArgs w, unsigned* key, unsigned* rank, unsigned* bcount) {
-  const int64_t n = (int64_t)*w.count_in;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const unsigned full = 0xFFFFFFFFu;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    unsigned k = 0xFFFFFFFFu;
-    if (i < n) {
-      const uint2 cb = w.cb_in[i];
-      const float4 td = w.td_in[i];
-      const float2 dd = w.dyz_in[i];
-      const unsigned ix = cb.x & 0xFFFFu, iy = cb.x >> 16, iz = cb.y & 0xFFFFu, b = cb.y >> 16;
-      const unsigned oct = (td.w < 0.f ? 1u : 0u) | (dd.x < 0.f ? 2u : 0u) | (dd.y < 0.f ? 4u : 0u);
-      const unsigned mort = spread3(ix >> 3) | (spread3(iy >> 3) << 1) | (spread3(iz >> 3) << 2);
-      k = (unsigned)a.boxes[b].bucket_off + ((mort << 3) | oct);
-      key[i] = k;
-    }
-    // packets of a warp that share a key take one atomic
-    const unsigned peers = __match_any_sync(full, k);
-    if (i < n) {
-      const int lane = threadIdx.x & 31;
-      const int leader = __ffs(peers) - 1;
-      unsigned r0 = 0;
-      if (lane == leader) r0 = atomicAdd(&bcount[k], (unsigned)__popc(peers));
-      r0 = __shfl_sync(peers, r0, leader);
-      rank[i] = r0 + __popc(peers & ((1u << lane) - 1u));
-    }
-  }
-}
-
 // exclusive scan of bcount into boff: 4096 keys per block, block sums, add
 __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* sh, unsigned* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -437,23 +497,15 @@ __global__ void k_scan_add(unsigned* out, const unsigned* bsum, int64_t n) {
   if (i < n) out[i] += bsum[i >> 12];
 }
 
-template <int NBT>
-__global__ void k_scatter(WFArgs w, const unsigned* key, const unsigned* rank, const unsigned* boff,
-                          int nb, int* err) {
-  const int64_t n = (int64_t)*w.count_in;
+// sorted position of record j: boff[key] + rank
+__global__ void k_perm(const unsigned* count, const unsigned* key, const unsigned* rank,
+                       const unsigned* boff, unsigned* perm, int* err) {
+  const int64_t n = (int64_t)*count;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *w.count_out = (unsigned)n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int64_t d = (int64_t)boff[key[i]] + rank[i];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const int64_t d = (int64_t)boff[key[j]] + rank[j];
     if (d >= n) { atomicOr(err, ERR_QUEUE); continue; }
-    w.cb_out[d] = w.cb_in[i];
-    w.td_out[d] = w.td_in[i];
-    w.dyz_out[d] = w.dyz_in[i];
-#pragma unroll
-    for (int j = 0; j < (NBT > 0 ? NBT : CRASH_MAX_BINS); ++j) {
-      if (NBT == 0 && j >= nb) break;
-      w.N_out[(int64_t)j * w.cap + d] = w.N_in[(int64_t)j * w.cap + i];
-    }
+    perm[d] = (unsigned)j;
   }
 }
 
@@ -461,13 +513,18 @@ __global__ void k_check_drained(const unsigned* count, int* err) {
   if (*count != 0u) atomicOr(err, ERR_WATCHDOG);
 }
 
-WFArgs wf_args(WF* wf, int in) {
+WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys) {
   WFArgs w;
   const int out = 1 - in;
-  w.cb_in = wf->cb[in]; w.td_in = wf->td[in]; w.dyz_in = wf->dyz[in]; w.N_in = wf->N[in];
-  w.cb_out = wf->cb[out]; w.td_out = wf->td[out]; w.dyz_out = wf->dyz[out]; w.N_out = wf->N[out];
+  w.rec_in = wf->rec[in];
+  w.rec_out = wf->rec[out];
   w.count_in = wf->count + in;
   w.count_out = wf->count + out;
+  w.perm = read_sorted ? wf->perm : nullptr;
+  w.key = write_keys ? wf->key : nullptr;
+  w.rank = write_keys ? wf->rank : nullptr;
+  w.bcount = wf->bcount;
+  w.rs = wf->rs;
   w.cap = wf->cap;
   return w;
 }
@@ -508,52 +565,48 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
   if (a.total_packets <= 0) return 0;
   if (!o.wavefront || wf->cap == 0) {
     // one thread per packet, traced to the end
-    WFArgs w = wf_args(wf, 0);
+    WFArgs w = wf_args(wf, 0, false, false);
     int64_t blocks = (a.total_packets + block - 1) / block;
     if (blocks > (int64_t)1 << 30) blocks = (int64_t)1 << 30;
     tic();
-    k_emit_mixed<NBT, HE, HEAT><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets, max_iter);
+    k_emit_mixed<NBT, HE, HEAT><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
+                                                                  max_iter, max_iter);
     toc();
     return 1;
   }
-  const int S = o.seg_per_iter > 0 ? o.seg_per_iter : 64;
-  const int R = o.resort_interval == 0 ? 2 : o.resort_interval;
+  const int S = o.seg_per_iter > 0 ? o.seg_per_iter : 32;
+  const int R = o.resort_interval == 0 ? 1 : o.resort_interval;
   const int passes = (max_iter + S - 1) / S;
   const int nscan = (int)((wf->n_keys + 4095) / 4096);
+  // the pass p (p >= 1) reads in sorted order when R > 0 and p % R == 0
+  auto sorted_pass = [&](int p) { return p >= 1 && p < passes && R > 0 && (p % R) == 0; };
   for (int64_t g0 = 0; g0 < a.total_packets; g0 += wf->cap) {
     const int64_t n = std::min<int64_t>(wf->cap, a.total_packets - g0);
-    int cur = 0;
+    int cur = 1;   // emission reads nothing and writes buffer 0
     cudaMemsetAsync(wf->count, 0, 4 * sizeof(unsigned), s);
-    {
-      WFArgs w = wf_args(wf, 1);     // emission writes survivors into buffer 0
-      w.count_out = wf->count + 0;
-      w.cb_out = wf->cb[0]; w.td_out = wf->td[0]; w.dyz_out = wf->dyz[0]; w.N_out = wf->N[0];
-      int64_t blocks = (n + block - 1) / block;
-      if (blocks > persistent * 4) blocks = persistent * 4;
-      tic();
-      k_emit_mixed<NBT, HE, HEAT><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, S);
-      toc();
-      ++launches;
-    }
-    for (int p = 1; p < passes; ++p) {
-      if (R > 0 && (p % R) == 0) {
-        WFArgs w = wf_args(wf, cur);
-        cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * wf->n_keys, s);
-        k_sort_keys<<<persistent, block, 0, s>>>(a, w, wf->key, wf->rank, wf->bcount);
-        k_scan_blocks<<<nscan, 1024, 0, s>>>(wf->bcount, wf->boff, wf->bsum, wf->n_keys);
-        k_scan_sums<<<1, 1024, 0, s>>>(wf->bsum, nscan);
-        k_scan_add<<<(unsigned)((wf->n_keys + 255) / 256), 256, 0, s>>>(wf->boff, wf->bsum, wf->n_keys);
-        k_scatter<NBT><<<persistent, block, 0, s>>>(w, wf->key, wf->rank, wf->boff, t.n_bins, a.err);
-        launches += 5;
-        cur = 1 - cur;
-      }
-      WFArgs w = wf_args(wf, cur);
+    for (int p = 0; p < passes; ++p) {
+      const bool next_sorted = sorted_pass(p + 1);
+      if (next_sorted) cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * wf->n_keys, s);
+      WFArgs w = wf_args(wf, cur, sorted_pass(p), next_sorted);
       cudaMemsetAsync(w.count_out, 0, sizeof(unsigned), s);
       tic();
-      k_pass_mixed<NBT, HE, HEAT><<<persistent, block, 0, s>>>(a, t, w, S);
+      if (p == 0) {
+        int64_t blocks = (n + block - 1) / block;
+        if (blocks > persistent * 4) blocks = persistent * 4;
+        k_emit_mixed<NBT, HE, HEAT><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, S, max_iter);
+      } else {
+        k_pass_mixed<NBT, HE, HEAT><<<persistent, block, 0, s>>>(a, t, w, S);
+      }
       toc();
       ++launches;
       cur = 1 - cur;
+      if (next_sorted) {
+        k_scan_blocks<<<nscan, 1024, 0, s>>>(wf->bcount, wf->boff, wf->bsum, wf->n_keys);
+        k_scan_sums<<<1, 1024, 0, s>>>(wf->bsum, nscan);
+        k_scan_add<<<(unsigned)((wf->n_keys + 255) / 256), 256, 0, s>>>(wf->boff, wf->bsum, wf->n_keys);
+        k_perm<<<persistent, block, 0, s>>>(wf->count + cur, wf->key, wf->rank, wf->boff, wf->perm, a.err);
+        launches += 4;
+      }
     }
     k_check_drained<<<1, 1, 0, s>>>(wf->count + cur, a.err);
     ++launches;
@@ -592,17 +645,14 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
   WF* w = new WF();
   w->cap = cap;
   w->nb = nb;
+  w->rs = ((32 + 8 * nb) + 15) / 16 * 16;
   w->n_keys = n_keys;
   cudaError_t e = cudaMalloc(&w->count, 4 * sizeof(unsigned));
   if (e == cudaSuccess && cap > 0) {
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-      e = cudaMalloc(&w->cb[b], sizeof(uint2) * cap);
-      if (e == cudaSuccess) e = cudaMalloc(&w->td[b], sizeof(float4) * cap);
-      if (e == cudaSuccess) e = cudaMalloc(&w->dyz[b], sizeof(float2) * cap);
-      if (e == cudaSuccess) e = cudaMalloc(&w->N[b], sizeof(long long) * cap * nb);
-    }
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&w->rec[b], (size_t)w->rs * cap);
     if (e == cudaSuccess) e = cudaMalloc(&w->key, sizeof(unsigned) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&w->rank, sizeof(unsigned) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&w->perm, sizeof(unsigned) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&w->bcount, sizeof(unsigned) * n_keys);
     if (e == cudaSuccess) e = cudaMalloc(&w->boff, sizeof(unsigned) * n_keys);
     if (e == cudaSuccess) e = cudaMalloc(&w->bsum, sizeof(unsigned) * 1024);
@@ -618,8 +668,8 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
 void wavefront_destroy(void* p) {
   WF* w = (WF*)p;
   if (!w) return;
-  void* ptrs[] = {w->count, w->key, w->rank, w->bcount, w->boff, w->bsum,
-                  w->cb[0], w->cb[1], w->td[0], w->td[1], w->dyz[0], w->dyz[1], w->N[0], w->N[1]};
+  void* ptrs[] = {w->count, w->key, w->rank, w->perm, w->bcount, w->boff, w->bsum,
+                  w->rec[0], w->rec[1]};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete w;
