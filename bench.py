@@ -285,8 +285,15 @@ def run_crash(args):
                 flush.fill_(1)
         g.step(w.dt_s, P)
 
-    for _ in range(args.warmup):
+    tuned = None
+    tuned_kw = {}
+    for k in range(args.warmup):
         one_step()
+        if k == 0 and prec == native.CRASH_MIXED and not args.no_autotune:
+            g.sync()
+            tuned = g.autotune(w.dt_s, [P])        # (block, crossings per pass, re-sort interval)
+            tuned_kw.update(block_size=tuned[0], seg_per_iter=tuned[1], resort_interval=tuned[2])
+            g.set_options(timing=1, **tuned_kw)
     g.sync()
     g.reset_kernel_time()
     tot0 = g.read(native.F_TOTALS)
@@ -338,7 +345,7 @@ def run_crash(args):
     # end-to-end through the C ABI with host buffers
     e2e = None
     if rank == 0 and not args.no_e2e:
-        g.set_options(timing=0)
+        g.set_options(timing=0, **tuned_kw)
         xh = np.empty(box.n ** 3, np.float64)
         bud = np.empty(8, np.int64)
         nb = len(box.bin_eV)
@@ -357,6 +364,29 @@ def run_crash(args):
             cr_e2e += int(bud[3])
         e2e = {"value": cr_e2e / t_e2e, "unit": "crossings/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
+
+    fp64 = None
+    if rank == 0 and prec == native.CRASH_MIXED and not args.no_fp64:
+        # the FP64 form on the same inputs, transport only, over a window of
+        # packet ids of every source (the FP64 pipe of this GPU is narrow)
+        g.close()
+        g = None
+        g64 = native.Grid(box, native.CRASH_FP64_PLAIN)
+        Ns = P // box.n_src
+        K = max(1, min(Ns, (1 << 21) // box.n_src))
+        g64.set_options(chemistry=0, timing=1, pkt_begin=0, pkt_end=K)
+        g64.step(w.dt_s, P)
+        g64.sync()
+        g64.reset_kernel_time()
+        t0 = g64.read(native.F_TOTALS)
+        g64.step(w.dt_s, P)
+        g64.sync()
+        t1 = g64.read(native.F_TOTALS)
+        ms64, _ = g64.kernel_time()
+        fp64 = {"value": float(t1[3] - t0[3]) / (ms64 * 1e-3), "unit": "crossings/s",
+                "sample": f"transport of packet ids [0,{K}) of each of the {box.n_src} sources, "
+                          f"first step, kernel time", "crossings": int(t1[3] - t0[3])}
+        g64.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -383,6 +413,9 @@ def run_crash(args):
                          "kernel_ms_per_launch": kms / max(1, klaunches)},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "fp64_plain": fp64,
+            "autotuned": {"block": tuned[0], "crossings_per_pass": tuned[1],
+                          "resort_interval": tuned[2]} if tuned else None,
             "gpu_launches": int(launches),
             "clocks": ck,
             "crossings_per_step": crossings / args.steps,
@@ -390,7 +423,8 @@ def run_crash(args):
             "chem_substeps_per_cell": float(tot1[7] - tot0[7]) / (args.steps * box.n ** 3),
         }
         print(json.dumps(line), flush=True)
-    g.close()
+    if g is not None:
+        g.close()
     if dist:
         dist.destroy_process_group()
 
@@ -401,7 +435,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crash", choices=["crash", "reference"])
-    ap.add_argument("--workload", default="hhe_bb_128")
+    ap.add_argument("--workload", default="lognormal_512_thin")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -462,7 +462,8 @@ static double cooling(const double* r, int mask, double ne, double nHI, double n
        fractions v (and eps T / |dT/dt|), the last allowed sub-step taking
        the remainder;
      * backward Euler for the H (2-state) and He (3-state) chains at fixed
-       T, with n_e taken at the end of the sub-step by 4 fixed-point passes;
+       T, with n_e taken at the end of the sub-step by at most 4 fixed-point
+       passes (fewer once n_e changes by less than 1e-12 relative);
      * temperature from the energy balance 1.5 k (n_tot T)' = H - Lambda,
        cooling linear in the new T (semi-implicit), photo-heating = mean
        excess energy per absorbed photon times the photo-ionisations of the
@@ -532,7 +533,10 @@ int or_chem_cell(or_chem_t* c, double dt) {
         y2n = d2 - c2 * y3n;
         y1n = d1 - c1 * y2n;
       }
-      nen = nH * xn + nHe * (y2n + 2.0 * y3n);
+      double ne_it = nH * xn + nHe * (y2n + 2.0 * y3n);
+      int converged = fabs(ne_it - nen) <= 1e-12 * ne_it;
+      nen = ne_it;
+      if (converged) break;
     }
     if (xn < 0.0) xn = 0.0;
     if (xn > 1.0) xn = 1.0;

@@ -19,7 +19,8 @@
 // more than eps * max(x, 1e-3) and T by more than eps * T; the last allowed
 // sub-step takes what remains):
 //   * backward Euler for the H (2-state) and He (3-state tridiagonal) chains
-//     at fixed T, with n_e at the end of the sub-step by 4 fixed-point passes;
+//     at fixed T, with n_e at the end of the sub-step by at most 4
+//     fixed-point passes (fewer once n_e changes by less than 1e-12);
 //   * fractions clamped to [0,1], He renormalised to unit sum;
 //   * 1.5 k (n_tot T)_new = 1.5 k (n_tot T)_old + h (H + C n_e T_cmb)
 //     - h (Lambda(T_old)/T_old + C n_e) T_new  (cooling linear in T_new).
@@ -171,15 +172,18 @@ __device__ int integrate_cell(const CellIn& c, double dt, double& x, double& y2,
         const double a11 = 1.0 + h * i1, a12 = -h * r2;
         const double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
         const double a32 = -h * i2, a33 = 1.0 + h * r3;
-        const double c1 = a12 / a11, d1 = y1 / a11;
-        const double m2 = a22 - a21 * c1;
-        const double c2 = a23 / m2, d2 = (y2 - a21 * d1) / m2;
-        const double m3 = a33 - a32 * c2;
-        y3n = (y3 - a32 * d2) / m3;
+        const double inv11 = 1.0 / a11;
+        const double c1 = a12 * inv11, d1 = y1 * inv11;
+        const double inv2 = 1.0 / (a22 - a21 * c1);
+        const double c2 = a23 * inv2, d2 = (y2 - a21 * d1) * inv2;
+        y3n = (y3 - a32 * d2) / (a33 - a32 * c2);
         y2n = d2 - c2 * y3n;
         y1n = d1 - c1 * y2n;
       }
-      nen = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
+      const double ne_it = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
+      const bool converged = fabs(ne_it - nen) <= 1e-12 * ne_it;
+      nen = ne_it;
+      if (converged) break;
     }
     xn = fmin(fmax(xn, 0.0), 1.0);
     if (he) {

@@ -154,7 +154,10 @@ enum { ALIVE = 0, ABSORBED = 1, ESCAPED = 2 };
 
 // Advance one packet by at most max_iter DDA steps.  tM* are the distances
 // (in cells, along the ray) from the current point to the next x/y/z face;
-// they are re-based at every step so that FP32 keeps their precision.
+// they are re-based at every step so that FP32 keeps their precision.  The
+// walk does not depend on the attenuation, so the next cell's absorbers are
+// requested before the current cell's bins are processed (one step of
+// software pipelining hides most of the gather latency).
 template <int NBT, bool HE, bool HEAT>
 __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx, float& tMy,
                                            float& tMz, const float dx, const float dy,
@@ -170,13 +173,33 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
   const int64_t coff = M->cell_off;
   const bool heat_box = HEAT && !M->isothermal;
   const float4* __restrict__ abs32 = reinterpret_cast<const float4*>(a.abs32);
-  for (int it = 0; it < max_iter; ++it) {
-    const float seg = fminf(tMx, fminf(tMy, tMz));
-    const int ax = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
+  if (max_iter <= 0) return ALIVE;
+  // current segment
+  float seg = fminf(tMx, fminf(tMy, tMz));
+  int ax = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
+  int64_t cell = coff + (ix + nx * (iy + ny * iz));
+  float4 ab = __ldg(abs32 + cell);
+  for (int it = 1;; ++it) {
+    // step the walk into the next cell and request its absorbers
+    tMx -= seg;
+    tMy -= seg;
+    tMz -= seg;
+    bool out;
+    if (ax == 0) { tMx = tDx; ix += sx; out = (unsigned)ix >= (unsigned)nx; }
+    else if (ax == 1) { tMy = tDy; iy += sy; out = (unsigned)iy >= (unsigned)ny; }
+    else { tMz = tDz; iz += sz; out = (unsigned)iz >= (unsigned)nz; }
+    float seg_n = 0.f;
+    int ax_n = 0;
+    int64_t cell_n = cell;
+    float4 ab_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!out) {
+      seg_n = fminf(tMx, fminf(tMy, tMz));
+      ax_n = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
+      cell_n = coff + (ix + nx * (iy + ny * iz));
+      ab_n = __ldg(abs32 + cell_n);
+    }
+    // attenuate and deposit in the current cell
     if (seg > 0.f) {
-      const int local = ix + nx * (iy + ny * iz);
-      const int64_t cell = coff + local;
-      const float4 ab = __ldg(abs32 + cell);
       const float l = seg * dl;
       const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
       long long Atot = 0, left = 0;
@@ -236,21 +259,13 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
       tl.crossings += 1;
       if (left == 0) return ABSORBED;
     }
-    tMx -= seg;
-    tMy -= seg;
-    tMz -= seg;
-    if (ax == 0) {
-      tMx = tDx; ix += sx;
-      if ((unsigned)ix >= (unsigned)nx) return ESCAPED;
-    } else if (ax == 1) {
-      tMy = tDy; iy += sy;
-      if ((unsigned)iy >= (unsigned)ny) return ESCAPED;
-    } else {
-      tMz = tDz; iz += sz;
-      if ((unsigned)iz >= (unsigned)nz) return ESCAPED;
-    }
+    if (out) return ESCAPED;
+    if (it >= max_iter) return ALIVE;
+    seg = seg_n;
+    ax = ax_n;
+    cell = cell_n;
+    ab = ab_n;
   }
-  return ALIVE;
 }
 
 // warp-aggregated append of surviving packets to the output queue
