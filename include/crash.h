@@ -170,6 +170,47 @@ crash_status crash_autotune(crash_ctx* ctx, double dt_s, const uint64_t* packets
 crash_status crash_free(crash_ctx* ctx);
 const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error */
 
+/* ---- Transport without device allocation.
+   The paper has no counterpart: this entry point exists for callers that
+   cannot call cudaMalloc (code inside another framework's memory pool or
+   under a fixed memory budget, plug-ins that may only use the buffers they
+   are handed).  It runs the mixed-form transport of one grid for one step
+   (emission, cell walk, attenuation, int64 deposition; no chemistry, no
+   re-sort) exactly as crash_step does for a context with the same grid,
+   sources and options, and allocates nothing: its scratch (packet queue of
+   65536 packets per pass buffer, per-source tables for at most
+   CRASH_NOALLOC_MAX_SOURCES sources, counters; about 21 MB) is a static
+   device array that every GPU loading the library holds until the process
+   exits.
+     grid: host struct; nx, ny, nz, box_cm, he_over_h, isothermal, caseB and
+       seed are used, the per-cell pointers are ignored.
+     pos_cells, ndot, bin_eV, bin_frac: host arrays as in crash_add_sources;
+       1 <= n_src <= CRASH_NOALLOC_MAX_SOURCES (larger counts are rejected
+       with CRASH_ERR_OVERFLOW), 1 <= n_bins <= 16.
+     dt_s, step_index, packets_per_step: as in crash_step (step_index is the
+       Philox step word); seg_per_pass: cells per wavefront pass (0 = 32).
+     absorbers_dev: device float[nx*ny*nz][4] = n_HI, n_HeI, n_HeII, 0 (cm^-3).
+     deposits_dev: device uint64[nx*ny*nz][4] (HI, HeI, HeII, heat); the
+       call ADDS its deposits, the caller zeroes the buffer for a fresh step.
+     budget_out: host int64[8], laid out as CRASH_F_BUDGET, written.
+     stream: a cudaStream_t (NULL: the default stream).
+   The first call on a device looks up the scratch address with that device
+   current (cudaGetSymbolAddress); make that first call before any stream
+   capture.  The call synchronises `stream` before it returns.  Every call
+   shares the one scratch array: calls that overlap on the GPU (from several
+   host threads, or on several streams of one device) race and must not be
+   issued.  Errors: CRASH_ERR_ARG / CRASH_ERR_OVERFLOW for rejected
+   arguments (nothing is launched), CRASH_ERR_CUDA, CRASH_ERR_TIMEOUT for a
+   device-side bound; crash_noalloc_last_error() gives the message. */
+#define CRASH_NOALLOC_MAX_SOURCES 1024
+crash_status crash_transport_noalloc(const crash_grid_desc* grid, int n_src, const double* pos_cells,
+                                     const double* ndot, int n_bins, const double* bin_eV,
+                                     const double* bin_frac, double dt_s, uint64_t step_index,
+                                     uint64_t packets_per_step, int seg_per_pass,
+                                     const float* absorbers_dev, unsigned long long* deposits_dev,
+                                     int64_t* budget_out, void* stream);
+const char* crash_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,7 @@ UNITS = [
     ("k_fp64.cu", ["-fmad=false"]),
     ("k_chem.cu", []),
     ("k_mixed.cu", []),
+    ("k_noalloc.cu", []),
 ]
 
 

@@ -301,7 +301,7 @@ extern "C" crash_status crash_init_grid(const crash_grid_desc* d, crash_ctx** ou
 }
 
 // ---------------------------------------------------------------- sources
-static void cross_sections(int nb, const double* E, BinTables& t, int& heatF) {
+void cross_sections(int nb, const double* E, BinTables& t, int& heatF) {
   double emax = 0.0;
   for (int j = 0; j < nb; ++j) {
     const double e = E[j];

@@ -109,6 +109,14 @@ typedef std::vector<std::pair<cudaEvent_t, cudaEvent_t>> EventPairs;
 int launch_trace_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o,
                        void* wf_state, int max_iter, cudaStream_t s, EventPairs* ev, int* ev_used);
 
+// Mixed-form wavefront over caller-provided record buffers (no allocation,
+// no re-sort): rec0/rec1 hold cap records each, count holds 4 counters.
+int launch_trace_mixed_external(const StepArgs& a, const BinTables& t, const crash_run_opts& o,
+                                char* rec0, char* rec1, unsigned* count, int64_t cap, int max_iter,
+                                cudaStream_t s);
+// cross sections, heating weights and heat exponent of a bin table (host)
+void cross_sections(int nb, const double* E, BinTables& t, int& heatF);
+
 // wavefront workspace (mixed form): capacity in packets, number of sort keys
 void* wavefront_create(int64_t capacity, int64_t n_keys, int n_bins, cudaError_t* err);
 void wavefront_destroy(void* w);

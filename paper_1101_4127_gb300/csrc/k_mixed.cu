@@ -656,6 +656,22 @@ int launch_trace_mixed(const StepArgs& a, const BinTables& t, const crash_run_op
   return r;
 }
 
+int launch_trace_mixed_external(const StepArgs& a, const BinTables& t, const crash_run_opts& o,
+                                char* rec0, char* rec1, unsigned* count, int64_t cap, int max_iter,
+                                cudaStream_t s) {
+  WF wf;                       // views the caller's buffers; owns nothing
+  wf.cap = cap;
+  wf.nb = t.n_bins;
+  wf.rs = ((32 + 8 * t.n_bins) + 15) / 16 * 16;
+  wf.rec[0] = rec0;
+  wf.rec[1] = rec1;
+  wf.count = count;
+  crash_run_opts oo = o;
+  oo.wavefront = 1;
+  oo.resort_interval = -1;     // no sort keys without their workspace
+  return launch_trace_mixed(a, t, oo, &wf, max_iter, s, nullptr, nullptr);
+}
+
 void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
   WF* w = new WF();
   w->cap = cap;

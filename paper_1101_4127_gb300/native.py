@@ -32,6 +32,7 @@ EXPORTED = [
     "crash_read_fields", "crash_read_fields_box", "crash_write_fields", "crash_write_fields_box",
     "crash_set_step_index", "crash_sync", "crash_kernel_time", "crash_reset_kernel_time",
     "crash_stream", "crash_launch_count", "crash_autotune", "crash_free", "crash_last_error",
+    "crash_transport_noalloc", "crash_noalloc_last_error",
 ]
 
 
@@ -91,12 +92,17 @@ def lib(build_if_missing: bool = True):
             L.crash_launch_count.restype = C.c_int64
             L.crash_autotune.argtypes = [P, C.c_double, C.POINTER(C.c_uint64), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.crash_transport_noalloc.argtypes = [
+                C.POINTER(crash_grid_desc), C.c_int, dp, dp, C.c_int, dp, dp, C.c_double, C.c_uint64,
+                C.c_uint64, C.c_int, P, P, C.POINTER(C.c_int64), P]
+            L.crash_noalloc_last_error.argtypes = []
+            L.crash_noalloc_last_error.restype = C.c_char_p
             L.crash_free.argtypes = [P]
             L.crash_last_error.argtypes = [P]
             L.crash_last_error.restype = C.c_char_p
             for name in EXPORTED:
                 if name not in ("crash_default_opts", "crash_stream", "crash_last_error",
-                                "crash_launch_count"):
+                                "crash_launch_count", "crash_noalloc_last_error"):
                     getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
