@@ -143,6 +143,17 @@ crash_status crash_read_fields_box(crash_ctx* ctx, int box, int field_id, void* 
 crash_status crash_write_fields(crash_ctx* ctx, int field_id, const void* host_in);
 crash_status crash_write_fields_box(crash_ctx* ctx, int box, int field_id, const void* host_in);
 
+/* Device-side checkpoint of the state fields (x_HII, x_HeII, x_HeIII, T)
+   and the step index, kept in a snapshot buffer owned by the context
+   (allocated by the first save).  op = CRASH_CKPT_SAVE stores the current
+   state; CRASH_CKPT_RESTORE_STATE copies the stored fields back and keeps
+   the step index running (the next step draws new directions);
+   CRASH_CKPT_RESTORE also restores the step index (the next step repeats
+   bit for bit).  Asynchronous on the context stream.  Restoring before any
+   save is CRASH_ERR_STATE. */
+enum { CRASH_CKPT_SAVE = 0, CRASH_CKPT_RESTORE_STATE = 1, CRASH_CKPT_RESTORE = 2 };
+crash_status crash_checkpoint(crash_ctx* ctx, int op);
+
 /* Step counter used as the Philox counter word (resume: restore the fields,
    then set the index of the next step). */
 crash_status crash_set_step_index(crash_ctx* ctx, uint64_t step);

@@ -74,6 +74,8 @@ struct crash_ctx {
   int64_t launches = 0;          // kernels enqueued so far
   int64_t graph_launches = 0;    // kernels inside the captured step graph
   int max_iter = 0;              // largest per-box DDA bound
+  double* snap = nullptr;        // checkpoint: 4 state fields
+  unsigned long long* snap_step = nullptr;
   int64_t n_keys = 0;            // wavefront re-sort keys over all boxes
   int wf_mode = -1;              // wavefront option the workspace was sized for
 };
@@ -120,7 +122,8 @@ static void release(crash_ctx* c) {
   if (c->wf) wavefront_destroy(c->wf);
   void* ptrs[] = {c->nH, c->xHII, c->xHeII, c->xHeIII, c->T, c->abs64, c->abs32, c->dep,
                   c->d_meta, c->budget, c->totals, c->step_dev, c->err, c->boxE, c->src_pos, c->src_ndot,
-                  c->src_frac, c->src_base, c->src_rem, c->src_pos32, c->src_cell};
+                  c->src_frac, c->src_base, c->src_rem, c->src_pos32, c->src_cell, c->snap,
+                  c->snap_step};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -447,6 +450,31 @@ extern "C" crash_status crash_set_options(crash_ctx* c, const crash_run_opts* o)
   if (o->seg_per_iter < 0) return set_err(c, CRASH_ERR_ARG, "seg_per_iter must be >= 0");
   c->opts = *o;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_checkpoint(crash_ctx* c, int op) {
+  if (!c) return CRASH_ERR_ARG;
+  cudaSetDevice(c->device);
+  const size_t n = (size_t)c->n_cells;
+  double* f[4] = {c->xHII, c->xHeII, c->xHeIII, c->T};
+  if (op == CRASH_CKPT_SAVE) {
+    if (!c->snap) {
+      CK(cudaMalloc(&c->snap, n * 8 * 4));
+      CK(cudaMalloc(&c->snap_step, 8));
+    }
+    for (int i = 0; i < 4; ++i)
+      CK(cudaMemcpyAsync(c->snap + i * n, f[i], n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->snap_step, c->step_dev, 8, cudaMemcpyDeviceToDevice, c->stream));
+    return CRASH_OK;
+  }
+  if (op != CRASH_CKPT_RESTORE_STATE && op != CRASH_CKPT_RESTORE)
+    return set_err(c, CRASH_ERR_ARG, "unknown checkpoint op");
+  if (!c->snap) return set_err(c, CRASH_ERR_STATE, "no checkpoint saved");
+  for (int i = 0; i < 4; ++i)
+    CK(cudaMemcpyAsync(f[i], c->snap + i * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (op == CRASH_CKPT_RESTORE)
+    CK(cudaMemcpyAsync(c->step_dev, c->snap_step, 8, cudaMemcpyDeviceToDevice, c->stream));
   return CRASH_OK;
 }
 

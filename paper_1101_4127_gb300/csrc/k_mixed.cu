@@ -96,17 +96,12 @@ __device__ __forceinline__ void flush_warp(const StepArgs& a, int b, Tally& t) {
   t = Tally{0, 0, 0, 0, 0};
 }
 
-// int64 <-> FP32 conversions done with integer ALU operations: on this GPU
-// the hardware 64-bit conversions issue to the FP64 pipe, which is narrow.
-// N in [0, 2^63) to FP32 by truncation to 24 significant bits (relative
-// error below 2^-23).
+// int64 <-> FP32 conversions without the hardware 64-bit conversions, which
+// on this GPU issue to the narrow FP64 pipe.  N in [0, 2^63) to FP32 from its
+// two 32-bit halves (relative error below 2^-23).
 __device__ __forceinline__ float ll_to_float(long long N) {
   const unsigned long long u = (unsigned long long)N;
-  if (u == 0ull) return 0.0f;
-  const int lz = __clzll(u);
-  const unsigned long long norm = u << lz;
-  const unsigned mant = (unsigned)(norm >> 40) & 0x7FFFFFu;
-  return __uint_as_float(((unsigned)(190 - lz) << 23) | mant);
+  return fmaf(__uint2float_rn((unsigned)(u >> 32)), 4294967296.0f, __uint2float_rn((unsigned)u));
 }
 
 // rint(x) for x in [0, 2^63), round half to even
@@ -118,9 +113,9 @@ __device__ __forceinline__ long long float_to_ll(float x) {
   return (long long)(m << ((int)(b >> 23) - 150));
 }
 
-// 1 - exp(-tau) for 0 < tau < 0.5 by its Taylor series to tau^8
+// (1 - exp(-tau)) / tau for 0 < tau < 0.5 by its Taylor series to tau^7
 // (truncation below 2e-8 relative)
-__device__ __forceinline__ float absorbed_fraction_small(float tau) {
+__device__ __forceinline__ float absorbed_over_tau(float tau) {
   float p = -1.0f / 40320.0f;
   p = fmaf(p, tau, 1.0f / 5040.0f);
   p = fmaf(p, tau, -1.0f / 720.0f);
@@ -129,22 +124,22 @@ __device__ __forceinline__ float absorbed_fraction_small(float tau) {
   p = fmaf(p, tau, 1.0f / 6.0f);
   p = fmaf(p, tau, -0.5f);
   p = fmaf(p, tau, 1.0f);
-  return tau * p;
+  return p;
 }
 
 // Absorbed count of one bin: for tau < 0.5 round N (1 - e^-tau), else round
 // the transmitted N e^-tau and take the difference, so that the smaller of
-// the two parts always carries ~1e-7 relative error.  Af is the absorbed
-// count in FP32 (for the species and heating weights).
-__device__ __forceinline__ long long absorb(long long N, float tau, float& Af) {
+// the two parts always carries ~1e-7 relative error.  q is the absorbed
+// count divided by tau in FP32: the species share of species s is q k_s.
+__device__ __forceinline__ long long absorb(long long N, float tau, float& q) {
   const float Nf = ll_to_float(N);
   if (tau < 0.5f) {
-    Af = Nf * absorbed_fraction_small(tau);
-    const long long A = float_to_ll(Af);
+    q = Nf * absorbed_over_tau(tau);
+    const long long A = float_to_ll(q * tau);
     return A > N ? N : A;
   }
   const float T = Nf * expf(-tau);
-  Af = Nf - T;
+  q = (Nf - T) * __fdividef(1.0f, tau);
   long long Np = float_to_ll(T);
   Np = Np > N ? N : Np;
   return N - Np;
@@ -216,23 +211,20 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
         }
         long long Nj = N[j];
         if (tau > 0.f && Nj > 0) {
-          float Af;
-          const long long A = absorb(Nj, tau, Af);
+          float q;
+          const long long A = absorb(Nj, tau, q);
           Nj -= A;
           N[j] = Nj;
           Atot += A;
-          if (HE || HEAT) {
-            const float inv = __frcp_rn(tau);
-            if (HE) {
-              fHeI += Af * (k1 * inv);
-              fHeII += Af * (k2 * inv);
-            }
-            if (HEAT) {
-              if (HE)
-                fheat += Af * ((k0 * t.wheat32[0][j] + k1 * t.wheat32[1][j] + k2 * t.wheat32[2][j]) * inv);
-              else
-                fheat += Af * t.wheat32[0][j];
-            }
+          if (HE) {
+            fHeI = fmaf(q, k1, fHeI);
+            fHeII = fmaf(q, k2, fHeII);
+          }
+          if (HEAT) {
+            if (HE)
+              fheat = fmaf(q, fmaf(k0, t.wheat32[0][j], fmaf(k1, t.wheat32[1][j], k2 * t.wheat32[2][j])), fheat);
+            else
+              fheat = fmaf(q * k0, t.wheat32[0][j], fheat);
           }
         }
         left |= Nj;

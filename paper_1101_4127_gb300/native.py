@@ -32,8 +32,9 @@ EXPORTED = [
     "crash_read_fields", "crash_read_fields_box", "crash_write_fields", "crash_write_fields_box",
     "crash_set_step_index", "crash_sync", "crash_kernel_time", "crash_reset_kernel_time",
     "crash_stream", "crash_launch_count", "crash_autotune", "crash_free", "crash_last_error",
-    "crash_transport_noalloc", "crash_noalloc_last_error",
+    "crash_transport_noalloc", "crash_noalloc_last_error", "crash_checkpoint",
 ]
+CKPT_SAVE, CKPT_RESTORE_STATE, CKPT_RESTORE = 0, 1, 2
 
 
 class crash_grid_desc(C.Structure):
@@ -83,6 +84,7 @@ def lib(build_if_missing: bool = True):
             L.crash_write_fields.argtypes = [P, C.c_int, P]
             L.crash_write_fields_box.argtypes = [P, C.c_int, C.c_int, P]
             L.crash_set_step_index.argtypes = [P, C.c_uint64]
+            L.crash_checkpoint.argtypes = [P, C.c_int]
             L.crash_sync.argtypes = [P]
             L.crash_kernel_time.argtypes = [P, dp, C.POINTER(C.c_int64)]
             L.crash_reset_kernel_time.argtypes = [P]
@@ -194,6 +196,9 @@ class Grid:
 
     def set_step_index(self, k):
         self._check(self.L.crash_set_step_index(self.ctx, int(k)))
+
+    def checkpoint(self, op=CKPT_SAVE):
+        self._check(self.L.crash_checkpoint(self.ctx, int(op)))
 
     def read(self, field, box=0):
         b = self.boxes[box]

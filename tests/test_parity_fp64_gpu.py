@@ -179,3 +179,26 @@ def test_graph_replay_matches_plain_launches():
         b.step(dt, P)
     for fg, _ in STATE_FIELDS + DEP_FIELDS:
         assert np.array_equal(a.read(fg), b.read(fg))
+
+
+def test_device_checkpoint_restore_repeats_step_bit_for_bit():
+    box = small_hhe_box((12, 10, 8), n_src=2, seed=80)
+    P = 2 * 1000
+    dt = 0.01 * inputs.MYR_S
+    for prec in (native.CRASH_FP64_PLAIN, native.CRASH_MIXED):
+        g = native.Grid(box, prec)
+        g.step(dt, P)
+        g.checkpoint(native.CKPT_SAVE)
+        g.step(dt, P)
+        first = [g.read(f) for f, _ in STATE_FIELDS + DEP_FIELDS]
+        g.checkpoint(native.CKPT_RESTORE)           # state and step index
+        g.step(dt, P)
+        again = [g.read(f) for f, _ in STATE_FIELDS + DEP_FIELDS]
+        for a, b in zip(first, again):
+            assert np.array_equal(a, b)
+        g.checkpoint(native.CKPT_RESTORE_STATE)     # state only: new directions
+        g.step(dt, P)
+        other = g.read(native.F_DEP_HI)
+        assert not np.array_equal(other, first[4])
+        b = g.read(native.F_BUDGET)
+        assert b[0] == b[1] + b[2]
