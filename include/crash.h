@@ -99,6 +99,8 @@ typedef struct {
   int wavefront;             /* mixed form: 1 = packet-queue wavefront, 0 = one thread per packet */
   int use_graph;             /* 1: capture each step in a CUDA graph and replay it */
   int timing;                /* 1: record CUDA events around the transport launches */
+  int reg_cap;               /* mixed form: 1 = transport kernels capped at 64 registers
+                                (more resident warps), 0 = uncapped (tuned/default) */
 } crash_run_opts;
 
 void crash_default_opts(crash_run_opts* o);

@@ -45,6 +45,7 @@ struct crash_ctx {
   unsigned long long* budget = nullptr;
   unsigned long long* totals = nullptr;   // [n_boxes][8] running sums of the budget
   unsigned long long* step_dev = nullptr;
+  unsigned long long* work = nullptr;
   int* err = nullptr;
   int* boxE = nullptr;
   double *src_pos = nullptr, *src_ndot = nullptr, *src_frac = nullptr;
@@ -121,7 +122,7 @@ static void release(crash_ctx* c) {
   }
   if (c->wf) wavefront_destroy(c->wf);
   void* ptrs[] = {c->nH, c->xHII, c->xHeII, c->xHeIII, c->T, c->abs64, c->abs32, c->dep,
-                  c->d_meta, c->budget, c->totals, c->step_dev, c->err, c->boxE, c->src_pos, c->src_ndot,
+                  c->d_meta, c->budget, c->totals, c->step_dev, c->work, c->err, c->boxE, c->src_pos, c->src_ndot,
                   c->src_frac, c->src_base, c->src_rem, c->src_pos32, c->src_cell, c->snap,
                   c->snap_step};
   for (void* p : ptrs)
@@ -271,7 +272,7 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
       {(void**)&c->xHeIII, n * 8}, {(void**)&c->T, n * 8}, {(void**)&c->dep, n * 32},
       {(void**)&c->d_meta, sizeof(BoxMeta) * n_boxes},
       {(void**)&c->budget, 64 * (size_t)n_boxes}, {(void**)&c->totals, 64 * (size_t)n_boxes},
-      {(void**)&c->step_dev, 8},
+      {(void**)&c->step_dev, 8}, {(void**)&c->work, 8},
       {(void**)&c->err, sizeof(int)}, {(void**)&c->boxE, sizeof(int) * n_boxes}};
   if (c->precision == CRASH_MIXED) allocs.push_back({(void**)&c->abs32, n * 16});
   else allocs.push_back({(void**)&c->abs64, n * 32});
@@ -518,6 +519,7 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
   a.abs64 = c->abs64; a.abs32 = c->abs32; a.dep = c->dep;
   a.n_cells_total = c->n_cells;
   a.budget = c->budget;
+  a.work = c->work;
   a.err = c->err;
   a.any_he = c->any_he; a.any_heat = c->any_heat;
   a.chemistry = c->opts.chemistry;
@@ -777,26 +779,29 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   crash_run_opts base = c->opts;
   crash_run_opts best = base;
   double best_ms = 1e300;
-  // trials trace a window of about 2^24 packets (one wavefront chunk or less)
+  // trials trace a window of about one wavefront chunk (2^26 packets) or less
   uint32_t win = 0xFFFFFFFFu;
   {
     int64_t tot = 0;
     for (int b = 0; b < c->n_boxes; ++b) tot += (int64_t)P[b];
-    if (tot > ((int64_t)1 << 24)) {
+    if (tot > ((int64_t)1 << 26)) {
       uint64_t mx = 1;
       for (int b = 0; b < c->n_boxes; ++b) mx = std::max<uint64_t>(mx, P[b] / (uint64_t)c->meta[b].n_src);
-      win = (uint32_t)std::max<uint64_t>(1, (uint64_t)((double)mx * (double)((int64_t)1 << 24) / (double)tot));
+      win = (uint32_t)std::max<uint64_t>(1, (uint64_t)((double)mx * (double)((int64_t)1 << 26) / (double)tot));
     }
   }
   std::vector<int> blocks = {64, 128, 256};
   std::vector<int> segs = {0};
   std::vector<int> resorts = {0};
+  std::vector<int> caps = {0};
   if (c->precision == CRASH_MIXED) {
     blocks = {128, 256};
     segs = {16, 32, 64};
-    resorts = {-1, 1, 2};
+    resorts = {1, 2};
+    caps = {0, 1};
   }
   crash_status st = CRASH_OK;
+  for (int cap : caps)
   for (int bs : blocks)
     for (int sg : segs)
       for (int rs : resorts) {
@@ -804,6 +809,7 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
         o.block_size = bs;
         o.seg_per_iter = sg;
         o.resort_interval = rs;
+        o.reg_cap = cap;
         o.pkt_begin = 0;
         o.pkt_end = win;
         o.chemistry = 0;
@@ -831,6 +837,7 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
           best.block_size = bs;
           best.seg_per_iter = sg;
           best.resort_interval = rs;
+          best.reg_cap = cap;
         }
       }
   c->opts = best;

@@ -82,6 +82,7 @@ struct StepArgs {
   int64_t n_cells_total;
   // budget [n_boxes][8] and device error word
   unsigned long long* budget;
+  unsigned long long* work;  // work counter of the persistent chemistry kernel
   int* err;
   // options
   int any_he;                // some box has helium (selects the H+He kernels)

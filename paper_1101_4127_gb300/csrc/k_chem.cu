@@ -26,6 +26,8 @@
 //     - h (Lambda(T_old)/T_old + C n_e) T_new  (cooling linear in T_new).
 #include <math.h>
 
+#include <algorithm>
+
 #include "crash_internal.cuh"
 #include "k_device.cuh"
 
@@ -113,170 +115,212 @@ struct CellIn {
   int iso, caseB, mask, max_sub;
 };
 
-// returns sub-steps; updates x (HII), y2 (HeII), y3 (HeIII), T
+// One sub-step of the cell integration; updates x (HII), y2 (HeII), y3
+// (HeIII), T and the remaining time rem (0 after the last sub-step).
 template <typename RT>
-__device__ int integrate_cell(const CellIn& c, double dt, double& x, double& y2, double& y3,
-                              double& T) {
+__device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, double& y3, double& T,
+                                        double& rem, int nsub) {
   const bool coll = (c.mask & 2) != 0, rec = (c.mask & 4) != 0, diel = (c.mask & 32) != 0;
   const bool he = c.nHe > 0.0;
-  double rem = dt;
-  int nsub = 0;
-  while (rem > 0.0) {
-    const Rates r = rates_at<RT>(T, c.caseB);
-    const double aH = rec ? r.aHII : 0.0;
-    const double aHe2 = rec ? r.aHeII + (diel ? r.adiel : 0.0) : 0.0;
-    const double aHe3 = rec ? r.aHeIII : 0.0;
-    const double bH = coll ? r.bHI : 0.0, bHe1 = coll ? r.bHeI : 0.0, bHe2 = coll ? r.bHeII : 0.0;
-    const double y1 = (1.0 - y2) - y3;
-    const double ne = c.nH * x + c.nHe * (y2 + 2.0 * y3);
-    // rates of change at the start of the sub-step (for the step size)
-    const double IH = c.GH + bH * ne, RH = aH * ne;
-    const double I1 = c.G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = c.G2 + bHe2 * ne, R3 = aHe3 * ne;
-    const double dx = IH * (1.0 - x) - RH * x;
-    const double dy1 = -I1 * y1 + R2 * y2;
-    const double dy3 = I2 * y2 - R3 * y3;
-    const double dy2 = -dy1 - dy3;
-    double h = rem;
-    {
-      const double val[5] = {1.0 - x, x, y1, y2, y3};
-      const double der[5] = {-dx, dx, dy1, dy2, dy3};
-      const int nv = he ? 5 : 2;
-      for (int i = 0; i < nv; ++i) {
-        const double fl = val[i] > 1e-3 ? val[i] : 1e-3;
-        const double ad = fabs(der[i]);
-        if (ad * h > c.eps * fl) h = c.eps * fl / ad;
-      }
+  const Rates r = rates_at<RT>(T, c.caseB);
+  const double aH = rec ? r.aHII : 0.0;
+  const double aHe2 = rec ? r.aHeII + (diel ? r.adiel : 0.0) : 0.0;
+  const double aHe3 = rec ? r.aHeIII : 0.0;
+  const double bH = coll ? r.bHI : 0.0, bHe1 = coll ? r.bHeI : 0.0, bHe2 = coll ? r.bHeII : 0.0;
+  const double y1 = (1.0 - y2) - y3;
+  const double ne = c.nH * x + c.nHe * (y2 + 2.0 * y3);
+  // rates of change at the start of the sub-step (for the step size)
+  const double IH = c.GH + bH * ne, RH = aH * ne;
+  const double I1 = c.G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = c.G2 + bHe2 * ne, R3 = aHe3 * ne;
+  const double dx = IH * (1.0 - x) - RH * x;
+  const double dy1 = -I1 * y1 + R2 * y2;
+  const double dy3 = I2 * y2 - R3 * y3;
+  const double dy2 = -dy1 - dy3;
+  double h = rem;
+  {
+    const double val[5] = {1.0 - x, x, y1, y2, y3};
+    const double der[5] = {-dx, dx, dy1, dy2, dy3};
+    const int nv = he ? 5 : 2;
+    for (int i = 0; i < nv; ++i) {
+      const double fl = val[i] > 1e-3 ? val[i] : 1e-3;
+      const double ad = fabs(der[i]);
+      if (ad * h > c.eps * fl) h = c.eps * fl / ad;
     }
-    const double ntot = c.nH + c.nHe + ne;
-    if (!c.iso) {
-      const double nHI = c.nH * (1.0 - x), nHII = c.nH * x;
-      const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2);
-      const double L = cooling_rate(r, c.mask, ne, nHI, nHII, c.nHe * y1, c.nHe * y2, c.nHe * y3) +
-                       c.ccomp * ne * (T - c.Tcmb);
-      const double dne = c.nH * dx + c.nHe * (dy2 + 2.0 * dy3);
-      const double dT = ((heat - L) / (1.5 * kB) - T * dne) / ntot;
-      const double adT = fabs(dT);
-      if (adT * h > c.eps * T) h = c.eps * T / adT;
-    }
-    if (nsub == c.max_sub - 1 || !(h < rem)) h = rem;
-    // implicit ionisation update
-    double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-      const double ih = c.GH + bH * nen, rh = aH * nen;
-      xn = (x + h * ih) / (1.0 + h * (ih + rh));
-      if (he) {
-        const double i1 = c.G1 + bHe1 * nen, r2 = aHe2 * nen;
-        const double i2 = c.G2 + bHe2 * nen, r3 = aHe3 * nen;
-        // tridiagonal (I - h Q) y_new = y_old, Thomas elimination
-        const double a11 = 1.0 + h * i1, a12 = -h * r2;
-        const double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
-        const double a32 = -h * i2, a33 = 1.0 + h * r3;
-        const double inv11 = 1.0 / a11;
-        const double c1 = a12 * inv11, d1 = y1 * inv11;
-        const double inv2 = 1.0 / (a22 - a21 * c1);
-        const double c2 = a23 * inv2, d2 = (y2 - a21 * d1) * inv2;
-        y3n = (y3 - a32 * d2) / (a33 - a32 * c2);
-        y2n = d2 - c2 * y3n;
-        y1n = d1 - c1 * y2n;
-      }
-      const double ne_it = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
-      const bool converged = fabs(ne_it - nen) <= 1e-12 * ne_it;
-      nen = ne_it;
-      if (converged) break;
-    }
-    xn = fmin(fmax(xn, 0.0), 1.0);
-    if (he) {
-      y1n = fmax(y1n, 0.0);
-      y2n = fmax(y2n, 0.0);
-      y3n = fmax(y3n, 0.0);
-      const double s = (y1n + y2n) + y3n;
-      y2n = y2n / s;
-      y3n = y3n / s;
-      y1n = (1.0 - y2n) - y3n;
-    }
-    const double ne2 = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
-    if (!c.iso) {
-      const double nHI = c.nH * (1.0 - xn), nHII = c.nH * xn;
-      const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n);
-      const double L = cooling_rate(r, c.mask, ne2, nHI, nHII, c.nHe * y1n, c.nHe * y2n,
-                                    c.nHe * y3n);
-      const double L1 = L / T;
-      const double Cc = c.ccomp * ne2;
-      const double ntot2 = c.nH + c.nHe + ne2;
-      T = (1.5 * kB * ntot * T + h * (heat + Cc * c.Tcmb)) / (1.5 * kB * ntot2 + h * (L1 + Cc));
-    }
-    x = xn;
-    y2 = y2n;
-    y3 = y3n;
-    rem = (h == rem) ? 0.0 : rem - h;
-    ++nsub;
   }
-  return nsub;
+  const double ntot = c.nH + c.nHe + ne;
+  if (!c.iso) {
+    const double nHI = c.nH * (1.0 - x), nHII = c.nH * x;
+    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2);
+    const double L = cooling_rate(r, c.mask, ne, nHI, nHII, c.nHe * y1, c.nHe * y2, c.nHe * y3) +
+                     c.ccomp * ne * (T - c.Tcmb);
+    const double dne = c.nH * dx + c.nHe * (dy2 + 2.0 * dy3);
+    const double dT = ((heat - L) / (1.5 * kB) - T * dne) / ntot;
+    const double adT = fabs(dT);
+    if (adT * h > c.eps * T) h = c.eps * T / adT;
+  }
+  if (nsub == c.max_sub - 1 || !(h < rem)) h = rem;
+  // implicit ionisation update
+  double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
+#pragma unroll 1
+  for (int it = 0; it < 4; ++it) {
+    const double ih = c.GH + bH * nen, rh = aH * nen;
+    xn = (x + h * ih) / (1.0 + h * (ih + rh));
+    if (he) {
+      const double i1 = c.G1 + bHe1 * nen, r2 = aHe2 * nen;
+      const double i2 = c.G2 + bHe2 * nen, r3 = aHe3 * nen;
+      // tridiagonal (I - h Q) y_new = y_old, Thomas elimination
+      const double a11 = 1.0 + h * i1, a12 = -h * r2;
+      const double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
+      const double a32 = -h * i2, a33 = 1.0 + h * r3;
+      const double inv11 = 1.0 / a11;
+      const double c1 = a12 * inv11, d1 = y1 * inv11;
+      const double inv2 = 1.0 / (a22 - a21 * c1);
+      const double c2 = a23 * inv2, d2 = (y2 - a21 * d1) * inv2;
+      y3n = (y3 - a32 * d2) / (a33 - a32 * c2);
+      y2n = d2 - c2 * y3n;
+      y1n = d1 - c1 * y2n;
+    }
+    const double ne_it = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
+    const bool converged = fabs(ne_it - nen) <= 1e-12 * ne_it;
+    nen = ne_it;
+    if (converged) break;
+  }
+  xn = fmin(fmax(xn, 0.0), 1.0);
+  if (he) {
+    y1n = fmax(y1n, 0.0);
+    y2n = fmax(y2n, 0.0);
+    y3n = fmax(y3n, 0.0);
+    const double s = (y1n + y2n) + y3n;
+    y2n = y2n / s;
+    y3n = y3n / s;
+    y1n = (1.0 - y2n) - y3n;
+  }
+  const double ne2 = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
+  if (!c.iso) {
+    const double nHI = c.nH * (1.0 - xn), nHII = c.nH * xn;
+    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n);
+    const double L = cooling_rate(r, c.mask, ne2, nHI, nHII, c.nHe * y1n, c.nHe * y2n,
+                                  c.nHe * y3n);
+    const double L1 = L / T;
+    const double Cc = c.ccomp * ne2;
+    const double ntot2 = c.nH + c.nHe + ne2;
+    T = (1.5 * kB * ntot * T + h * (heat + Cc * c.Tcmb)) / (1.5 * kB * ntot2 + h * (L1 + Cc));
+  }
+  x = xn;
+  y2 = y2n;
+  y3 = y3n;
+  rem = (h == rem) ? 0.0 : rem - h;
 }
+
 
 }  // namespace
 
+// Per-cell inputs of the integration, from the step's deposits (Sec. 2
+// coupling: photo-ionisation rate per frozen absorber, mean excess energy).
+__device__ __forceinline__ void load_cell(const StepArgs& a, int64_t i, int b, CellIn& c, double& x,
+                                          double& y2, double& y3, double& T) {
+  const BoxMeta* M = a.boxes + b;
+  const int E = a.box_E[b];
+  const double q = ldexp(1.0, E);
+  const double qE = ldexp(1.0, E + M->heatF) * eV;
+  const double V = (M->dl * M->dl) * M->dl;
+  x = a.xHII[i]; y2 = a.xHeII[i]; y3 = a.xHeIII[i]; T = a.T[i];
+  c.nH = (double)a.nH[i];
+  c.nHe = c.nH * M->he;
+  const double NHI = (c.nH * (1.0 - x)) * V;
+  const double NHeI = (c.nHe * ((1.0 - y2) - y3)) * V;
+  const double NHeII = (c.nHe * y2) * V;
+  const ulonglong2 d01 = reinterpret_cast<const ulonglong2*>(a.dep)[2 * i];
+  const ulonglong2 d23 = reinterpret_cast<const ulonglong2*>(a.dep)[2 * i + 1];
+  const long long dHI = (long long)d01.x, dHeI = (long long)d01.y;
+  const long long dHeII = (long long)d23.x, dE = (long long)d23.y;
+  c.GH = NHI > 0 ? ((double)dHI * q) / (a.dt * NHI) : 0.0;
+  c.G1 = NHeI > 0 ? ((double)dHeI * q) / (a.dt * NHeI) : 0.0;
+  c.G2 = NHeII > 0 ? ((double)dHeII * q) / (a.dt * NHeII) : 0.0;
+  const long long nabs = (dHI + dHeI) + dHeII;
+  c.eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
+  c.iso = M->isothermal;
+  c.caseB = M->caseB;
+  c.Tcmb = M->T_cmb;
+  c.mask = a.cool_mask;
+  if (M->T_cmb > 0 && (a.cool_mask & 16)) {
+    const double t2 = M->T_cmb * M->T_cmb;
+    c.ccomp = 4.0 * sigmaT * aRad * (t2 * t2) * kB / (mE * cLight);
+  } else {
+    c.ccomp = 0.0;
+  }
+  c.eps = a.chem_eps;
+  c.max_sub = a.chem_max_sub;
+}
+
+// Persistent kernel: every lane integrates one cell at a time, one sub-step
+// per loop turn, and takes the next unclaimed cell (warp-aggregated atomic
+// on a step counter) as soon as its cell is done.  Cells need from one to
+// thousands of sub-steps, so handing out work per lane keeps the warps full
+// instead of waiting for the slowest cell of a fixed group of 32.
 template <typename RT>
-__global__ void __launch_bounds__(128) k_chemistry(StepArgs a) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_chemistry(StepArgs a, unsigned long long* next_cell) {
+  const unsigned full = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  const int64_t n = a.n_cells_total;
+  int64_t i = -1;
+  int b = -1, tb = -1;
+  CellIn c;
+  double x = 0, y2 = 0, y3 = 0, T = 0, rem = 0;
+  int nsub = 0;
   unsigned long long subs = 0;
-  int b = -1;
-  if (i < a.n_cells_total) {
-    b = box_of_cell(a.boxes, a.n_boxes, i);
-    const BoxMeta* M = a.boxes + b;
-    const int E = a.box_E[b];
-    const double q = ldexp(1.0, E);
-    const double qE = ldexp(1.0, E + M->heatF) * eV;
-    const double V = (M->dl * M->dl) * M->dl;
-    double x = a.xHII[i], y2 = a.xHeII[i], y3 = a.xHeIII[i], T = a.T[i];
-    CellIn c;
-    c.nH = (double)a.nH[i];
-    c.nHe = c.nH * M->he;
-    const double NHI = (c.nH * (1.0 - x)) * V;
-    const double NHeI = (c.nHe * ((1.0 - y2) - y3)) * V;
-    const double NHeII = (c.nHe * y2) * V;
-    const ulonglong2 d01 = reinterpret_cast<const ulonglong2*>(a.dep)[2 * i];
-    const ulonglong2 d23 = reinterpret_cast<const ulonglong2*>(a.dep)[2 * i + 1];
-    const long long dHI = (long long)d01.x, dHeI = (long long)d01.y;
-    const long long dHeII = (long long)d23.x, dE = (long long)d23.y;
-    c.GH = NHI > 0 ? ((double)dHI * q) / (a.dt * NHI) : 0.0;
-    c.G1 = NHeI > 0 ? ((double)dHeI * q) / (a.dt * NHeI) : 0.0;
-    c.G2 = NHeII > 0 ? ((double)dHeII * q) / (a.dt * NHeII) : 0.0;
-    const long long nabs = (dHI + dHeI) + dHeII;
-    c.eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
-    c.iso = M->isothermal;
-    c.caseB = M->caseB;
-    c.Tcmb = M->T_cmb;
-    c.mask = a.cool_mask;
-    if (M->T_cmb > 0 && (a.cool_mask & 16)) {
-      const double t2 = M->T_cmb * M->T_cmb;
-      c.ccomp = 4.0 * sigmaT * aRad * (t2 * t2) * kB / (mE * cLight);
-    } else {
-      c.ccomp = 0.0;
+  bool need = true, exhausted = false;
+  while (true) {
+    const unsigned m = __ballot_sync(full, need && !exhausted);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(next_cell, (unsigned long long)__popc(m));
+      base = __shfl_sync(full, base, leader);
+      if (need && !exhausted) {
+        i = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+        if (i >= n) {
+          exhausted = true;
+          i = -1;
+        } else {
+          b = box_of_cell(a.boxes, a.n_boxes, i);
+          if (b != tb) {
+            if (tb >= 0 && subs) atomicAdd(a.budget + tb * 8 + 7, subs);
+            tb = b;
+            subs = 0;
+          }
+          load_cell(a, i, b, c, x, y2, y3, T);
+          rem = a.dt;
+          nsub = 0;
+          need = false;
+        }
+      }
     }
-    c.eps = a.chem_eps;
-    c.max_sub = a.chem_max_sub;
-    subs = (unsigned long long)integrate_cell<RT>(c, a.dt, x, y2, y3, T);
-    a.xHII[i] = x;
-    a.xHeII[i] = y2;
-    a.xHeIII[i] = y3;
-    a.T[i] = T;
+    const bool active = !need;
+    if (!__any_sync(full, active)) break;
+    if (active) {
+      substep<RT>(c, x, y2, y3, T, rem, nsub);
+      ++nsub;
+      if (!(rem > 0.0)) {
+        a.xHII[i] = x;
+        a.xHeII[i] = y2;
+        a.xHeIII[i] = y3;
+        a.T[i] = T;
+        subs += (unsigned long long)nsub;
+        need = true;
+      }
+    }
   }
-  // sub-step tally per box (warp sum when the warp's cells share a box)
-  int b0 = __shfl_sync(0xFFFFFFFFu, b, 0);
-  bool uniform = __all_sync(0xFFFFFFFFu, b == b0 || b < 0);
-  if (uniform) {
-    subs = warp_sum_u64(subs);
-    if ((threadIdx.x & 31) == 0 && b0 >= 0 && subs) atomicAdd(a.budget + b0 * 8 + 7, subs);
-  } else if (b >= 0) {
-    atomicAdd(a.budget + b * 8 + 7, subs);
-  }
+  if (tb >= 0 && subs) atomicAdd(a.budget + tb * 8 + 7, subs);
 }
 
 void launch_chemistry(const StepArgs& a, cudaStream_t s) {
   if (a.n_cells_total <= 0) return;
-  int64_t blocks = (a.n_cells_total + 127) / 128;
-  if (a.fp32_rates) k_chemistry<float><<<(unsigned)blocks, 128, 0, s>>>(a);
-  else k_chemistry<double><<<(unsigned)blocks, 128, 0, s>>>(a);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = std::min<int64_t>((a.n_cells_total + 127) / 128, (int64_t)sms * 8);
+  cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
+  if (a.fp32_rates) k_chemistry<float><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
+  else k_chemistry<double><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
 }

@@ -65,7 +65,8 @@ struct WFArgs {
 };
 
 struct Tally {
-  unsigned long long emitted, absorbed, escaped, crossings, packets;
+  unsigned long long emitted, absorbed, escaped;
+  unsigned crossings, packets;       // per thread between flushes: far below 2^32
 };
 
 __device__ __forceinline__ void flush_warp(const StepArgs& a, int b, Tally& t) {
@@ -75,25 +76,25 @@ __device__ __forceinline__ void flush_warp(const StepArgs& a, int b, Tally& t) {
     t.emitted = warp_sum_u64(t.emitted);
     t.absorbed = warp_sum_u64(t.absorbed);
     t.escaped = warp_sum_u64(t.escaped);
-    t.crossings = warp_sum_u64(t.crossings);
-    t.packets = warp_sum_u64(t.packets);
+    const unsigned long long cr = warp_sum_u64(t.crossings);
+    const unsigned long long pk = warp_sum_u64(t.packets);
     if ((threadIdx.x & 31) == 0 && b0 >= 0) {
       unsigned long long* g = a.budget + b0 * 8;
       if (t.emitted) atomicAdd(g + 0, t.emitted);
       if (t.absorbed) atomicAdd(g + 1, t.absorbed);
       if (t.escaped) atomicAdd(g + 2, t.escaped);
-      if (t.crossings) atomicAdd(g + 3, t.crossings);
-      if (t.packets) atomicAdd(g + 4, t.packets);
+      if (cr) atomicAdd(g + 3, cr);
+      if (pk) atomicAdd(g + 4, pk);
     }
   } else if (b >= 0) {
     unsigned long long* g = a.budget + b * 8;
     if (t.emitted) atomicAdd(g + 0, t.emitted);
     if (t.absorbed) atomicAdd(g + 1, t.absorbed);
     if (t.escaped) atomicAdd(g + 2, t.escaped);
-    if (t.crossings) atomicAdd(g + 3, t.crossings);
-    if (t.packets) atomicAdd(g + 4, t.packets);
+    if (t.crossings) atomicAdd(g + 3, (unsigned long long)t.crossings);
+    if (t.packets) atomicAdd(g + 4, (unsigned long long)t.packets);
   }
-  t = Tally{0, 0, 0, 0, 0};
+  t = Tally{0, 0, 0, 0u, 0u};
 }
 
 // int64 <-> FP32 conversions without the hardware 64-bit conversions, which
@@ -360,13 +361,15 @@ __device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& 
 }
 
 // ------------------------------------------------------------------ emission
-template <int NBT, bool HE, bool HEAT>
-__global__ void __launch_bounds__(256) k_emit_mixed(StepArgs a, BinTables t, WFArgs w, int64_t g0,
+// MINB = 4 caps the kernels at 64 registers (more resident warps to hide the
+// gather latency); MINB = 1 leaves the register count to the compiler.
+template <int NBT, bool HE, bool HEAT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables t, WFArgs w, int64_t g0,
                                                    int64_t n, int S, int max_steps_all) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const uint32_t step = (uint32_t)*a.step_dev;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  Tally tl{0, 0, 0, 0, 0};
+  Tally tl{0, 0, 0, 0u, 0u};
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t i = base + threadIdx.x;
     int b = -1;
@@ -414,12 +417,12 @@ __global__ void __launch_bounds__(256) k_emit_mixed(StepArgs a, BinTables t, WFA
 }
 
 // ------------------------------------------------------------------ passes
-template <int NBT, bool HE, bool HEAT>
-__global__ void __launch_bounds__(256) k_pass_mixed(StepArgs a, BinTables t, WFArgs w, int S) {
+template <int NBT, bool HE, bool HEAT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pass_mixed(StepArgs a, BinTables t, WFArgs w, int S) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const int64_t n = (int64_t)*w.count_in;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  Tally tl{0, 0, 0, 0, 0};
+  Tally tl{0, 0, 0, 0u, 0u};
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t j = base + threadIdx.x;
     int b = -1;
@@ -576,8 +579,12 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
     int64_t blocks = (a.total_packets + block - 1) / block;
     if (blocks > (int64_t)1 << 30) blocks = (int64_t)1 << 30;
     tic();
-    k_emit_mixed<NBT, HE, HEAT><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
-                                                                  max_iter, max_iter);
+    if (o.reg_cap)
+      k_emit_mixed<NBT, HE, HEAT, 4><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
+                                                                       max_iter, max_iter);
+    else
+      k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
+                                                                       max_iter, max_iter);
     toc();
     return 1;
   }
@@ -600,9 +607,13 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
       if (p == 0) {
         int64_t blocks = (n + block - 1) / block;
         if (blocks > persistent * 4) blocks = persistent * 4;
-        k_emit_mixed<NBT, HE, HEAT><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, S, max_iter);
+        if (o.reg_cap)
+          k_emit_mixed<NBT, HE, HEAT, 4><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, S, max_iter);
+        else
+          k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, S, max_iter);
       } else {
-        k_pass_mixed<NBT, HE, HEAT><<<persistent, block, 0, s>>>(a, t, w, S);
+        if (o.reg_cap) k_pass_mixed<NBT, HE, HEAT, 4><<<persistent, block, 0, s>>>(a, t, w, S);
+        else k_pass_mixed<NBT, HE, HEAT, 1><<<persistent, block, 0, s>>>(a, t, w, S);
       }
       toc();
       ++launches;

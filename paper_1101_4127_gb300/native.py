@@ -51,7 +51,8 @@ class crash_run_opts(C.Structure):
     _fields_ = [("chemistry", C.c_int), ("pkt_begin", C.c_uint32), ("pkt_end", C.c_uint32),
                 ("chem_eps", C.c_double), ("chem_max_sub", C.c_int), ("cool_mask", C.c_int),
                 ("block_size", C.c_int), ("seg_per_iter", C.c_int), ("resort_interval", C.c_int),
-                ("wavefront", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int)]
+                ("wavefront", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
+                ("reg_cap", C.c_int)]
 
 
 def library_path() -> str:
