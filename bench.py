@@ -51,6 +51,8 @@ def workload(name):
         return inputs.lognormal_128(), native.CRASH_MIXED
     if name == "lognormal_128_thin":
         return inputs.lognormal_128(thin=True), native.CRASH_MIXED
+    if name == "batch_64":
+        return inputs.batch_64(), native.CRASH_MIXED
     if name == "lognormal_256_thin":      # profiling case: a few GB on the device
         return inputs.lognormal_512(n=256, n_src=2000, packets=4_000_000, thin=True), native.CRASH_MIXED
     if name == "lognormal_512_thin":
@@ -264,16 +266,22 @@ def run_crash(args):
     dev = torch.device("cuda", local)
 
     w, prec = workload(args.workload)
-    box = w.boxes[0]
-    box.seed = box.seed + rank          # independent replica per rank
-    P = w.packets_per_step[0]
+    boxes = w.boxes
+    box = boxes[0]
+    for bx in boxes:
+        bx.seed = bx.seed + rank          # independent replica per rank
     if args.packets:
-        P = max(box.n_src, args.packets // box.n_src * box.n_src)
-        w.packets_per_step[0] = P
-    g = native.Grid(box, prec)
-    g.set_options(timing=1)
+        w.packets_per_step = [max(bx.n_src, args.packets // bx.n_src * bx.n_src) for bx in boxes]
+    Plist = list(w.packets_per_step)
+    P = Plist[0]
+    batch = len(boxes) > 1
+    step_arg = Plist if batch else P
+    ncell_all = sum(bx.n ** 3 for bx in boxes)
+    g = native.Grid(boxes, prec)
+    graph = bool(args.graph)
+    g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0)
     stream = torch.cuda.ExternalStream(g.stream(), device=dev)
-    state_bytes = box.n ** 3 * (4 + 4 * 8 + 32 + (32 if prec == native.CRASH_FP64_PLAIN else 16))
+    state_bytes = ncell_all * (4 + 4 * 8 + 32 + (32 if prec == native.CRASH_FP64_PLAIN else 16))
     l2_bytes = 129 * 2**20
     flush = None
     if state_bytes < 2 * l2_bytes:
@@ -292,7 +300,13 @@ def run_crash(args):
                 flush.fill_(1)
         if hold:
             g.checkpoint(native.CKPT_RESTORE_STATE)
-        g.step(w.dt_s, P)
+        g.step(w.dt_s, step_arg)
+
+    def totals():
+        t = np.zeros(8, np.int64)
+        for i in range(len(boxes)):
+            t += g.read(native.F_TOTALS, i)
+        return t
 
     tuned = None
     tuned_kw = {}
@@ -300,12 +314,13 @@ def run_crash(args):
         one_step()
         if k == 0 and prec == native.CRASH_MIXED and not args.no_autotune:
             g.sync()
-            tuned = g.autotune(w.dt_s, [P])        # (block, crossings per pass, re-sort interval)
-            tuned_kw.update(block_size=tuned[0], seg_per_iter=tuned[1], resort_interval=tuned[2])
-            g.set_options(timing=1, **tuned_kw)
+            tuned = g.autotune(w.dt_s, Plist)   # block, crossings per pass, re-sort, reg cap
+            tuned_kw.update(block_size=tuned[0], seg_per_iter=tuned[1], resort_interval=tuned[2],
+                            reg_cap=tuned[3])
+            g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0, **tuned_kw)
     g.sync()
     g.reset_kernel_time()
-    tot0 = g.read(native.F_TOTALS)
+    tot0 = totals()
     launches0 = g.launch_count()
     clocks = ClockSampler(local)
     if dist:
@@ -323,9 +338,11 @@ def run_crash(args):
         dist.barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    tot1 = g.read(native.F_TOTALS)
+    tot1 = totals()
     launches = g.launch_count() - launches0
     kms, klaunches = g.kernel_time()
+    if graph:      # no per-launch events inside a replayed graph: time whole steps
+        kms, klaunches = ms, args.steps
     crossings = int(tot1[3] - tot0[3])
     if dist:
         t = torch.tensor([ms, float(crossings)], dtype=torch.float64, device=dev)
@@ -368,7 +385,8 @@ def run_crash(args):
                 a_[:] = val
                 state_in.append(a_)
         nb = len(box.bin_eV)
-        h2d = box.n_src * (3 + 1 + nb) * 8 + nb * 8 + sum(a_.nbytes for a_ in state_in)
+        h2d = sum(bx.n_src for bx in boxes) * (3 + 1 + nb) * 8 + len(boxes) * nb * 8 + \
+            sum(a_.nbytes for a_ in state_in)
         d2h = xh.nbytes + bud.nbytes
         t_e2e = 0.0
         cr_e2e = 0
@@ -379,17 +397,21 @@ def run_crash(args):
             t0 = time.perf_counter()
             for f_, a_ in zip(fields, state_in):
                 g._check(g.L.crash_write_fields(g.ctx, f_, a_.ctypes.data))
-            g.add_sources(box.src_pos, box.src_ndot, box.bin_eV, box.bin_frac)
-            g.step(w.dt_s, P)
+            for i_, bx in enumerate(boxes):
+                g.add_sources(bx.src_pos, bx.src_ndot, bx.bin_eV, bx.bin_frac, box=i_)
+            g.step(w.dt_s, step_arg)
             g._check(g.L.crash_read_fields(g.ctx, native.F_XHII, xh.ctypes.data))
-            g._check(g.L.crash_read_fields(g.ctx, native.F_BUDGET, bud.ctypes.data))
+            cr_step = 0
+            for i_ in range(len(boxes)):
+                g._check(g.L.crash_read_fields_box(g.ctx, i_, native.F_BUDGET, bud.ctypes.data))
+                cr_step += int(bud[3])
             t_e2e += time.perf_counter() - t0
-            cr_e2e += int(bud[3])
+            cr_e2e += cr_step
         e2e = {"value": cr_e2e / t_e2e, "unit": "crossings/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     fp64 = None
-    if rank == 0 and prec == native.CRASH_MIXED and not args.no_fp64:
+    if rank == 0 and prec == native.CRASH_MIXED and not args.no_fp64 and not batch:
         # the FP64 form on the same inputs, transport only, over a window of
         # packet ids of every source (the FP64 pipe of this GPU is narrow)
         g.close()
@@ -423,8 +445,11 @@ def run_crash(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == native.CRASH_FP64_PLAIN else "f32+i64",
             "data": "synthetic",
-            "config": {"workload": w.name, "grid": box.n, "sources": box.n_src,
-                       "packets_per_step": P, "bins": len(box.bin_eV),
+            "config": {"workload": w.name,
+                       "grid": [bx.n for bx in boxes] if batch else box.n,
+                       "sources": sum(bx.n_src for bx in boxes),
+                       "packets_per_step": sum(Plist), "bins": len(box.bin_eV),
+                       "cuda_graph": graph,
                        "precision": "fp64" if prec == native.CRASH_FP64_PLAIN else "mixed",
                        "l2": "flushed between steps (256 MiB write)" if flush is not None
                              else "state larger than L2",
@@ -434,18 +459,19 @@ def run_crash(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "transport", "bytes_per_crossing": bx,
+                         "kernel": "whole step (graph replay)" if graph else "transport",
+                         "bytes_per_crossing": bx,
                          "kernel_ms_per_launch": kms / max(1, klaunches)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "fp64_plain": fp64,
             "autotuned": {"block": tuned[0], "crossings_per_pass": tuned[1],
-                          "resort_interval": tuned[2]} if tuned else None,
+                          "resort_interval": tuned[2], "reg_cap": tuned[3]} if tuned else None,
             "gpu_launches": int(launches),
             "clocks": ck,
             "crossings_per_step": crossings / args.steps,
             "transport_ms_per_step": kms / args.steps,
-            "chem_substeps_per_cell": float(tot1[7] - tot0[7]) / (args.steps * box.n ** 3),
+            "chem_substeps_per_cell": float(tot1[7] - tot0[7]) / (args.steps * ncell_all),
         }
         print(json.dumps(line), flush=True)
     if g is not None:
@@ -462,6 +488,7 @@ def main():
     ap.add_argument("--impl", default="crash", choices=["crash", "reference"])
     ap.add_argument("--workload", default="lognormal_512_thin")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="replay each step as a CUDA graph")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -174,11 +174,14 @@ void* crash_stream(crash_ctx* ctx);
    (graph replays count the kernels inside the graph). */
 int64_t crash_launch_count(crash_ctx* ctx);
 
-/* Autotuner: times trial steps over block size, crossings per pass and
-   re-sort interval on the current state (which is saved and restored) and
-   stores the fastest in the context's options; returns the chosen values. */
+/* Autotuner: times transport-only trial steps over block size, crossings
+   per pass, re-sort interval and register cap (mixed form) on the current
+   state, over a window of about one wavefront chunk of packet ids; the state
+   and the step index are restored afterwards.  Stores the fastest in the
+   context's options and returns the chosen values (outputs may be NULL). */
 crash_status crash_autotune(crash_ctx* ctx, double dt_s, const uint64_t* packets_per_box,
-                            int* block_size, int* seg_per_iter, int* resort_interval);
+                            int* block_size, int* seg_per_iter, int* resort_interval,
+                            int* reg_cap);
 
 crash_status crash_free(crash_ctx* ctx);
 const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error */

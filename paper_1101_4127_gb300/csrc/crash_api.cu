@@ -762,7 +762,7 @@ extern "C" crash_status crash_reset_kernel_time(crash_ctx* c) {
 
 // ---------------------------------------------------------------- autotune
 extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* P, int* block,
-                                       int* seg, int* resort) {
+                                       int* seg, int* resort, int* reg_cap) {
   if (!c || !P) return CRASH_ERR_ARG;
   cudaSetDevice(c->device);
   // save the state and the step index so that trials leave no trace
@@ -853,5 +853,6 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   if (block) *block = best.block_size;
   if (seg) *seg = best.seg_per_iter;
   if (resort) *resort = best.resort_interval;
+  if (reg_cap) *reg_cap = best.reg_cap;
   return CRASH_OK;
 }

@@ -137,3 +137,21 @@ def test_mixed_full_size_512_window_against_oracle():
     a = g.read(native.F_DEP_HI).astype(np.float64)
     b = o.read(oracle.F_DEP_HI).astype(np.float64)
     assert abs(a.sum() - b.sum()) <= 1e-5 * b.sum()
+
+
+def test_batch_64_recipe_graph_equals_separate_boxes():
+    """The 64-box batch recipe (sizes from {32,48,64,96,128}^3, 1-100 sources,
+    log-uniform packet counts) at 1/1000 of its packets, stepped as one batch
+    replayed from a CUDA graph: every box equals the same box run alone."""
+    w = inputs.batch_64(scale=1e-3)
+    dt = w.dt_s
+    g = native.Grid(w.boxes, MIXED)
+    g.set_options(use_graph=1, seg_per_iter=16, resort_interval=1)
+    for _ in range(2):
+        g.step(dt, w.packets_per_step)
+    for i in (0, 7, 31, 63):
+        single = _run(w.boxes[i], w.packets_per_step[i], 2, dt, seg_per_iter=32, resort_interval=2)
+        for x, y in zip(_fields(g, i), _fields(single)):
+            assert np.array_equal(x, y), i
+    tot = sum(int(g.read(native.F_BUDGET, i)[0]) for i in range(len(w.boxes)))
+    assert tot > 0
