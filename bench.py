@@ -316,7 +316,7 @@ def run_crash(args):
             g.sync()
             tuned = g.autotune(w.dt_s, Plist)   # block, crossings per pass, re-sort, reg cap
             tuned_kw.update(block_size=tuned[0], seg_per_iter=tuned[1], resort_interval=tuned[2],
-                            reg_cap=tuned[3])
+                            reg_cap=tuned[3], tile=tuned[4])
             g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0, **tuned_kw)
     g.sync()
     g.reset_kernel_time()
@@ -466,7 +466,8 @@ def run_crash(args):
             "e2e": e2e,
             "fp64_plain": fp64,
             "autotuned": {"block": tuned[0], "crossings_per_pass": tuned[1],
-                          "resort_interval": tuned[2], "reg_cap": tuned[3]} if tuned else None,
+                          "resort_interval": tuned[2], "reg_cap": tuned[3],
+                          "tile": tuned[4]} if tuned else None,
             "gpu_launches": int(launches),
             "clocks": ck,
             "crossings_per_step": crossings / args.steps,

@@ -101,6 +101,9 @@ typedef struct {
   int timing;                /* 1: record CUDA events around the transport launches */
   int reg_cap;               /* mixed form: 1 = transport kernels capped at 64 registers
                                 (more resident warps), 0 = uncapped (tuned/default) */
+  int tile;                  /* mixed form: 1 = tile passes (packets sorted into 16^3-cell
+                                tiles, absorbers and deposits of a tile staged in shared
+                                memory); 0 = passes of seg_per_iter cells over global memory */
 } crash_run_opts;
 
 void crash_default_opts(crash_run_opts* o);
@@ -175,13 +178,14 @@ void* crash_stream(crash_ctx* ctx);
 int64_t crash_launch_count(crash_ctx* ctx);
 
 /* Autotuner: times transport-only trial steps over block size, crossings
-   per pass, re-sort interval and register cap (mixed form) on the current
-   state, over a window of about one wavefront chunk of packet ids; the state
-   and the step index are restored afterwards.  Stores the fastest in the
-   context's options and returns the chosen values (outputs may be NULL). */
+   per pass, re-sort interval, register cap and tile passes (mixed form) on
+   the current state, over a window of about one wavefront chunk of packet
+   ids; the state and the step index are restored afterwards.  Stores the
+   fastest in the context's options and returns the chosen values (outputs
+   may be NULL). */
 crash_status crash_autotune(crash_ctx* ctx, double dt_s, const uint64_t* packets_per_box,
                             int* block_size, int* seg_per_iter, int* resort_interval,
-                            int* reg_cap);
+                            int* reg_cap, int* tile);
 
 crash_status crash_free(crash_ctx* ctx);
 const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error */

@@ -78,6 +78,8 @@ struct crash_ctx {
   double* snap = nullptr;        // checkpoint: 4 state fields
   unsigned long long* snap_step = nullptr;
   int64_t n_keys = 0;            // wavefront re-sort keys over all boxes
+  int64_t n_tile_keys = 0;       // tile-pass keys over all boxes
+  int max_tiles = 0;             // bound on the tiles one packet crosses
   int wf_mode = -1;              // wavefront option the workspace was sized for
 };
 
@@ -250,6 +252,19 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
     c->max_iter = std::max(c->max_iter, m.max_iter);
   }
   c->n_keys = keys;
+  // tile-pass keys: 16^3-cell tiles times 8 octants (fewer than the 8^3 keys)
+  int64_t tkeys = 0;
+  for (int i = 0; i < n_boxes; ++i) {
+    BoxMeta& m = c->meta[i];
+    int cmax = std::max(std::max((m.nx + 15) / 16, (m.ny + 15) / 16), (m.nz + 15) / 16);
+    int bits = 0;
+    while ((1 << bits) < cmax) ++bits;
+    m.tile_bits = bits;
+    m.tile_off = tkeys;
+    tkeys += (int64_t)8 << (3 * bits);
+    c->max_tiles = std::max(c->max_tiles, (m.nx + 15) / 16 + (m.ny + 15) / 16 + (m.nz + 15) / 16 + 3);
+  }
+  c->n_tile_keys = tkeys;
   auto fail = [&](crash_status st) { release(c); return st; };
   if (c->precision == CRASH_MIXED) {
     for (int i = 0; i < n_boxes; ++i)
@@ -520,6 +535,8 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
   a.n_cells_total = c->n_cells;
   a.budget = c->budget;
   a.work = c->work;
+  a.n_tile_keys = c->n_tile_keys;
+  a.max_tiles = c->max_tiles;
   a.err = c->err;
   a.any_he = c->any_he; a.any_heat = c->any_heat;
   a.chemistry = c->opts.chemistry;
@@ -762,7 +779,7 @@ extern "C" crash_status crash_reset_kernel_time(crash_ctx* c) {
 
 // ---------------------------------------------------------------- autotune
 extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* P, int* block,
-                                       int* seg, int* resort, int* reg_cap) {
+                                       int* seg, int* resort, int* reg_cap, int* tile) {
   if (!c || !P) return CRASH_ERR_ARG;
   cudaSetDevice(c->device);
   // save the state and the step index so that trials leave no trace
@@ -801,45 +818,51 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
     caps = {0, 1};
   }
   crash_status st = CRASH_OK;
+  struct Trial { int bs, sg, rs, cap, tile; };
+  std::vector<Trial> trials;
   for (int cap : caps)
-  for (int bs : blocks)
-    for (int sg : segs)
-      for (int rs : resorts) {
-        crash_run_opts o = base;
-        o.block_size = bs;
-        o.seg_per_iter = sg;
-        o.resort_interval = rs;
-        o.reg_cap = cap;
-        o.pkt_begin = 0;
-        o.pkt_end = win;
-        o.chemistry = 0;
-        o.use_graph = 0;
-        o.timing = 0;
-        c->opts = o;
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        st = crash_step_batch(c, dt, P);                 // warm-up
-        if (st == CRASH_OK) {
-          cudaEventRecord(e0, c->stream);
-          st = crash_step_batch(c, dt, P);
-          cudaEventRecord(e1, c->stream);
-        }
-        cudaStreamSynchronize(c->stream);
-        float ms = 0.f;
-        if (st == CRASH_OK) cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        if (st != CRASH_OK) break;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = base;
-          best.block_size = bs;
-          best.seg_per_iter = sg;
-          best.resort_interval = rs;
-          best.reg_cap = cap;
-        }
-      }
+    for (int bs : blocks)
+      for (int sg : segs)
+        for (int rs : resorts) trials.push_back({bs, sg, rs, cap, 0});
+  if (c->precision == CRASH_MIXED) trials.push_back({256, 0, 1, 0, 1});
+  for (const Trial& tr : trials) {
+    crash_run_opts o = base;
+    o.block_size = tr.bs;
+    o.seg_per_iter = tr.sg;
+    o.resort_interval = tr.rs;
+    o.reg_cap = tr.cap;
+    o.tile = tr.tile;
+    o.pkt_begin = 0;
+    o.pkt_end = win;
+    o.chemistry = 0;
+    o.use_graph = 0;
+    o.timing = 0;
+    c->opts = o;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    st = crash_step_batch(c, dt, P);                 // warm-up
+    if (st == CRASH_OK) {
+      cudaEventRecord(e0, c->stream);
+      st = crash_step_batch(c, dt, P);
+      cudaEventRecord(e1, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    float ms = 0.f;
+    if (st == CRASH_OK) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != CRASH_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = base;
+      best.block_size = tr.bs;
+      best.seg_per_iter = tr.sg;
+      best.resort_interval = tr.rs;
+      best.reg_cap = tr.cap;
+      best.tile = tr.tile;
+    }
+  }
   c->opts = best;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   cudaMemcpy(c->xHII, save, n * 8, cudaMemcpyDeviceToDevice);
@@ -854,5 +877,6 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   if (seg) *seg = best.seg_per_iter;
   if (resort) *resort = best.resort_interval;
   if (reg_cap) *reg_cap = best.reg_cap;
+  if (tile) *tile = best.tile;
   return CRASH_OK;
 }

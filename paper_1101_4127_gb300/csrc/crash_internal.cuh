@@ -44,6 +44,10 @@ struct BoxMeta {
   // morton(ix >> 3, iy >> 3, iz >> 3) (bucket_bits bits per axis) * 8 + octant
   int64_t bucket_off;
   int bucket_bits;
+  // tile passes: keys of this box start at tile_off; a key is
+  // morton(ix >> 4, iy >> 4, iz >> 4) (tile_bits bits per axis) * 8 + octant
+  int64_t tile_off;
+  int tile_bits;
   int max_iter;            // nx + ny + nz + 3: bound on DDA steps of one packet
 };
 
@@ -83,6 +87,8 @@ struct StepArgs {
   // budget [n_boxes][8] and device error word
   unsigned long long* budget;
   unsigned long long* work;  // work counter of the persistent chemistry kernel
+  int64_t n_tile_keys;       // tile-pass sort keys over all boxes
+  int max_tiles;             // bound on the tiles one packet crosses
   int* err;
   // options
   int any_he;                // some box has helium (selects the H+He kernels)

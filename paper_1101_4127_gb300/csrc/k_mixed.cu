@@ -48,6 +48,7 @@ struct WF {
   unsigned* bcount = nullptr;            // [n_keys]
   unsigned* boff = nullptr;              // [n_keys]
   unsigned* bsum = nullptr;              // [1024]
+  unsigned* tiles = nullptr;             // [n_keys / 8] non-empty tiles of a tile pass
   int64_t n_keys = 0;
 };
 
@@ -61,6 +62,7 @@ struct WFArgs {
   unsigned* rank;
   unsigned* bcount;
   int rs;
+  int tile;                  // keys of 16^3-cell tiles (tile passes) instead of 8^3 buckets
   int64_t cap;
 };
 
@@ -148,117 +150,188 @@ __device__ __forceinline__ long long absorb(long long N, float tau, float& q) {
 
 enum { ALIVE = 0, ABSORBED = 1, ESCAPED = 2 };
 
+// Attenuation and deposition in one crossed cell (Sec. 2, Eq. 1) for a
+// segment of seg cells: updates the packet's bins N and returns the absorbed
+// total; the species and heating deposits of the cell come back in d*.
+template <int NBT, bool HE, bool HEAT>
+__device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 ab, long long* N,
+                                                    int nb, const BinTables& t, long long& dHI,
+                                                    long long& dHeI, long long& dHeII, long long& dE,
+                                                    long long& left) {
+  const float l = seg * dl;
+  const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
+  long long Atot = 0;
+  left = 0;
+  float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
+#pragma unroll
+  for (int j = 0; j < (NBT > 0 ? NBT : CRASH_MAX_BINS); ++j) {
+    if (NBT == 0 && j >= nb) break;
+    const float k0 = tHI * t.sigma32[0][j];
+    float tau = k0, k1 = 0.f, k2 = 0.f;
+    if (HE) {
+      k1 = tHeI * t.sigma32[1][j];
+      k2 = tHeII * t.sigma32[2][j];
+      tau = (k0 + k1) + k2;
+    }
+    long long Nj = N[j];
+    if (tau > 0.f && Nj > 0) {
+      float q;
+      const long long A = absorb(Nj, tau, q);
+      Nj -= A;
+      N[j] = Nj;
+      Atot += A;
+      if (HE) {
+        fHeI = fmaf(q, k1, fHeI);
+        fHeII = fmaf(q, k2, fHeII);
+      }
+      if (HEAT) {
+        if (HE)
+          fheat = fmaf(q, fmaf(k0, t.wheat32[0][j], fmaf(k1, t.wheat32[1][j], k2 * t.wheat32[2][j])), fheat);
+        else
+          fheat = fmaf(q * k0, t.wheat32[0][j], fheat);
+      }
+    }
+    left |= Nj;
+  }
+  dHeI = 0;
+  dHeII = 0;
+  dE = 0;
+  if (Atot) {
+    if (HE) {
+      dHeI = float_to_ll(fHeI);
+      dHeI = dHeI > Atot ? Atot : dHeI;
+      dHeII = float_to_ll(fHeII);
+      dHeII = dHeII > Atot - dHeI ? Atot - dHeI : dHeII;
+    }
+    if (HEAT) dE = float_to_ll(fheat);
+  }
+  dHI = Atot - dHeI - dHeII;
+  return Atot;
+}
+
+// Where a walk reads absorbers and adds deposits: the grid in global memory
+// (gathers and int64 reductions in L2) ...
+struct GlobalCells {
+  const float4* abs;
+  unsigned long long* dep;
+  int64_t coff;
+  int nx, ny;
+  __device__ __forceinline__ int64_t index(int ix, int iy, int iz) const {
+    return coff + (ix + nx * (iy + ny * iz));
+  }
+  __device__ __forceinline__ float4 load(int64_t c) const { return __ldg(abs + c); }
+  __device__ __forceinline__ void add(int64_t c, long long a0, long long a1, long long a2, long long e) const {
+    unsigned long long* dp = dep + 4 * c;
+    if (a0) atomicAdd(dp + 0, (unsigned long long)a0);
+    if (a1) atomicAdd(dp + 1, (unsigned long long)a1);
+    if (a2) atomicAdd(dp + 2, (unsigned long long)a2);
+    if (e) atomicAdd(dp + 3, (unsigned long long)e);
+  }
+};
+
+// ... or one 16^3-cell tile staged in shared memory (absorbers copied in,
+// deposits accumulated with shared atomics and flushed once per tile visit)
+struct TileCells {
+  const float4* abs;               // shared, [16][16][16]
+  unsigned long long* dep;         // shared, [16][16][16][4]
+  int x0, y0, z0;
+  __device__ __forceinline__ int64_t index(int ix, int iy, int iz) const {
+    return (ix - x0) + 16 * ((iy - y0) + 16 * (iz - z0));
+  }
+  __device__ __forceinline__ float4 load(int64_t c) const { return abs[c]; }
+  __device__ __forceinline__ void add(int64_t c, long long a0, long long a1, long long a2, long long e) const {
+    unsigned long long* dp = dep + 4 * c;
+    if (a0) atomicAdd(dp + 0, (unsigned long long)a0);
+    if (a1) atomicAdd(dp + 1, (unsigned long long)a1);
+    if (a2) atomicAdd(dp + 2, (unsigned long long)a2);
+    if (e) atomicAdd(dp + 3, (unsigned long long)e);
+  }
+};
+
 // Advance one packet by at most max_iter DDA steps.  tM* are the distances
 // (in cells, along the ray) from the current point to the next x/y/z face;
 // they are re-based at every step so that FP32 keeps their precision.  The
 // walk does not depend on the attenuation, so the next cell's absorbers are
 // requested before the current cell's bins are processed (one step of
-// software pipelining hides most of the gather latency).
-template <int NBT, bool HE, bool HEAT>
-__device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx, float& tMy,
-                                           float& tMz, const float dx, const float dy,
-                                           const float dz, long long* N, const BoxMeta* M,
-                                           const StepArgs& a, const BinTables& t, const int nb,
-                                           const int max_iter, Tally& tl) {
+// software pipelining hides most of the gather latency).  With TILE the walk
+// also stops (alive) when it steps out of the box [tx0,tx0+ex) x ... .
+template <int NBT, bool HE, bool HEAT, bool TILE, class Cells>
+__device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float& tMy, float& tMz,
+                                    const float dx, const float dy, const float dz, long long* N,
+                                    const BoxMeta* M, const Cells& cells, const BinTables& t,
+                                    const int nb, const int max_iter, Tally& tl, int tx0 = 0,
+                                    int ty0 = 0, int tz0 = 0, int ex = 0, int ey = 0, int ez = 0) {
   const int nx = M->nx, ny = M->ny, nz = M->nz;
   const float tDx = dx != 0.f ? 1.0f / fabsf(dx) : INFINITY;
   const float tDy = dy != 0.f ? 1.0f / fabsf(dy) : INFINITY;
   const float tDz = dz != 0.f ? 1.0f / fabsf(dz) : INFINITY;
   const int sx = dx > 0.f ? 1 : -1, sy = dy > 0.f ? 1 : -1, sz = dz > 0.f ? 1 : -1;
   const float dl = M->dlf;
-  const int64_t coff = M->cell_off;
   const bool heat_box = HEAT && !M->isothermal;
-  const float4* __restrict__ abs32 = reinterpret_cast<const float4*>(a.abs32);
   if (max_iter <= 0) return ALIVE;
   // current segment
   float seg = fminf(tMx, fminf(tMy, tMz));
   int ax = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
-  int64_t cell = coff + (ix + nx * (iy + ny * iz));
-  float4 ab = __ldg(abs32 + cell);
+  int64_t cell = cells.index(ix, iy, iz);
+  float4 ab = cells.load(cell);
   for (int it = 1;; ++it) {
     // step the walk into the next cell and request its absorbers
     tMx -= seg;
     tMy -= seg;
     tMz -= seg;
-    bool out;
-    if (ax == 0) { tMx = tDx; ix += sx; out = (unsigned)ix >= (unsigned)nx; }
-    else if (ax == 1) { tMy = tDy; iy += sy; out = (unsigned)iy >= (unsigned)ny; }
-    else { tMz = tDz; iz += sz; out = (unsigned)iz >= (unsigned)nz; }
+    bool out, leave;
+    if (ax == 0) {
+      tMx = tDx; ix += sx; out = (unsigned)ix >= (unsigned)nx;
+      leave = TILE ? (unsigned)(ix - tx0) >= (unsigned)ex : out;
+    } else if (ax == 1) {
+      tMy = tDy; iy += sy; out = (unsigned)iy >= (unsigned)ny;
+      leave = TILE ? (unsigned)(iy - ty0) >= (unsigned)ey : out;
+    } else {
+      tMz = tDz; iz += sz; out = (unsigned)iz >= (unsigned)nz;
+      leave = TILE ? (unsigned)(iz - tz0) >= (unsigned)ez : out;
+    }
     float seg_n = 0.f;
     int ax_n = 0;
     int64_t cell_n = cell;
     float4 ab_n = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!out) {
+    if (!leave) {
       seg_n = fminf(tMx, fminf(tMy, tMz));
       ax_n = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
-      cell_n = coff + (ix + nx * (iy + ny * iz));
-      ab_n = __ldg(abs32 + cell_n);
+      cell_n = cells.index(ix, iy, iz);
+      ab_n = cells.load(cell_n);
     }
     // attenuate and deposit in the current cell
     if (seg > 0.f) {
-      const float l = seg * dl;
-      const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
-      long long Atot = 0, left = 0;
-      float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
-#pragma unroll
-      for (int j = 0; j < (NBT > 0 ? NBT : CRASH_MAX_BINS); ++j) {
-        if (NBT == 0 && j >= nb) break;
-        const float k0 = tHI * t.sigma32[0][j];
-        float tau = k0, k1 = 0.f, k2 = 0.f;
-        if (HE) {
-          k1 = tHeI * t.sigma32[1][j];
-          k2 = tHeII * t.sigma32[2][j];
-          tau = (k0 + k1) + k2;
-        }
-        long long Nj = N[j];
-        if (tau > 0.f && Nj > 0) {
-          float q;
-          const long long A = absorb(Nj, tau, q);
-          Nj -= A;
-          N[j] = Nj;
-          Atot += A;
-          if (HE) {
-            fHeI = fmaf(q, k1, fHeI);
-            fHeII = fmaf(q, k2, fHeII);
-          }
-          if (HEAT) {
-            if (HE)
-              fheat = fmaf(q, fmaf(k0, t.wheat32[0][j], fmaf(k1, t.wheat32[1][j], k2 * t.wheat32[2][j])), fheat);
-            else
-              fheat = fmaf(q * k0, t.wheat32[0][j], fheat);
-          }
-        }
-        left |= Nj;
-      }
+      long long dHI, dHeI, dHeII, dE, left;
+      const long long Atot = cell_attenuate<NBT, HE, HEAT>(seg, dl, ab, N, nb, t, dHI, dHeI, dHeII,
+                                                           dE, left);
       if (Atot) {
-        long long dHeI = 0, dHeII = 0;
-        if (HE) {
-          dHeI = float_to_ll(fHeI);
-          dHeI = dHeI > Atot ? Atot : dHeI;
-          dHeII = float_to_ll(fHeII);
-          dHeII = dHeII > Atot - dHeI ? Atot - dHeI : dHeII;
-        }
-        const long long dHI = Atot - dHeI - dHeII;
-        unsigned long long* dp = a.dep + 4 * cell;
-        if (dHI) atomicAdd(dp + 0, (unsigned long long)dHI);
-        if (dHeI) atomicAdd(dp + 1, (unsigned long long)dHeI);
-        if (dHeII) atomicAdd(dp + 2, (unsigned long long)dHeII);
-        if (heat_box) {
-          const long long h = float_to_ll(fheat);
-          if (h) atomicAdd(dp + 3, (unsigned long long)h);
-        }
+        cells.add(cell, dHI, dHeI, dHeII, heat_box ? dE : 0ll);
         tl.absorbed += (unsigned long long)Atot;
       }
       tl.crossings += 1;
       if (left == 0) return ABSORBED;
     }
     if (out) return ESCAPED;
+    if (TILE && leave) return ALIVE;
     if (it >= max_iter) return ALIVE;
     seg = seg_n;
     ax = ax_n;
     cell = cell_n;
     ab = ab_n;
   }
+}
+
+// the walk over the grid in global memory
+template <int NBT, bool HE, bool HEAT>
+__device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx, float& tMy,
+                                           float& tMz, const float dx, const float dy,
+                                           const float dz, long long* N, const BoxMeta* M,
+                                           const StepArgs& a, const BinTables& t, const int nb,
+                                           const int max_iter, Tally& tl) {
+  GlobalCells cells{reinterpret_cast<const float4*>(a.abs32), a.dep, M->cell_off, M->nx, M->ny};
+  return walk<NBT, HE, HEAT, false>(ix, iy, iz, tMx, tMy, tMz, dx, dy, dz, N, M, cells, t, nb,
+                                    max_iter, tl);
 }
 
 // warp-aggregated append of surviving packets to the output queue
@@ -284,13 +357,16 @@ __device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every 
   return v;
 }
 
-// sort key: Morton order of the packet's 8^3-cell bucket, then direction octant
+// sort key: Morton order of the packet's 8^3-cell bucket (16^3-cell tile for
+// tile passes), then direction octant
 __device__ __forceinline__ unsigned sort_key(const BoxMeta* boxes, int box, int ix, int iy, int iz,
-                                             float dx, float dy, float dz) {
+                                             float dx, float dy, float dz, int tile) {
   const unsigned oct = (dx < 0.f ? 1u : 0u) | (dy < 0.f ? 2u : 0u) | (dz < 0.f ? 4u : 0u);
-  const unsigned mort = spread3((unsigned)ix >> 3) | (spread3((unsigned)iy >> 3) << 1) |
-                        (spread3((unsigned)iz >> 3) << 2);
-  return (unsigned)boxes[box].bucket_off + ((mort << 3) | oct);
+  const int sh = tile ? 4 : 3;
+  const unsigned mort = spread3((unsigned)ix >> sh) | (spread3((unsigned)iy >> sh) << 1) |
+                        (spread3((unsigned)iz >> sh) << 2);
+  const unsigned base = tile ? (unsigned)boxes[box].tile_off : (unsigned)boxes[box].bucket_off;
+  return base + ((mort << 3) | oct);
 }
 
 template <int NBT>
@@ -346,7 +422,7 @@ __device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& 
   }
   if (ok) store_record<NBT>(w.rec_out, w.rs, slot, ix, iy, iz, box, tMx, tMy, tMz, dx, dy, dz, N, nb);
   if (w.key) {
-    const unsigned k = ok ? sort_key(a.boxes, box, ix, iy, iz, dx, dy, dz) : 0xFFFFFFFFu;
+    const unsigned k = ok ? sort_key(a.boxes, box, ix, iy, iz, dx, dy, dz, w.tile) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
     if (ok) {
       const int lane = threadIdx.x & 31;
@@ -519,12 +595,142 @@ __global__ void k_perm(const unsigned* count, const unsigned* key, const unsigne
   }
 }
 
+// ------------------------------------------------------------------ tiles
+constexpr int kTileMinPackets = 256;   // sparser tiles walk over global memory
+constexpr int kTileBlock = 512;
+constexpr size_t kTileSmem = 4096 * sizeof(float4) + 4096 * 4 * sizeof(unsigned long long);
+
+__device__ __forceinline__ unsigned compact3(unsigned v) {   // every third bit -> 10 bits
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030C30C3u;
+  v = (v | (v >> 4)) & 0x0300F00Fu;
+  v = (v | (v >> 8)) & 0x030000FFu;
+  v = (v | (v >> 16)) & 0x3FFu;
+  return v;
+}
+
+__device__ __forceinline__ int box_of_tile(const BoxMeta* b, int n, unsigned T) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned)(b[mid].tile_off >> 3) <= T) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// packets of tile T occupy sorted positions [boff[8T], boff[8T+8])
+__device__ __forceinline__ unsigned tile_end(const unsigned* boff, const unsigned* count, int64_t n_keys,
+                                             unsigned T) {
+  return (8 * (int64_t)T + 8 < n_keys) ? boff[8 * (int64_t)T + 8] : *count;
+}
+
+// list of the tiles that hold packets (any order: results do not depend on it)
+__global__ void k_tile_list(const unsigned* boff, const unsigned* count, int64_t n_keys, unsigned* list,
+                            unsigned* nlist) {
+  const int64_t ntiles = n_keys / 8;
+  for (int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; T < ntiles;
+       T += (int64_t)gridDim.x * blockDim.x) {
+    if (tile_end(boff, count, n_keys, (unsigned)T) > boff[8 * T]) list[atomicAdd(nlist, 1u)] = (unsigned)T;
+  }
+}
+
+// One tile pass: a block takes the next non-empty tile, copies its 16^3
+// absorbers into shared memory, walks every packet of the tile until it
+// leaves the tile (or is absorbed or escapes), accumulating the deposits in
+// shared memory, then adds them to the grid once.  Tiles with few packets
+// are walked over global memory instead.  Survivors go to the output queue
+// with the key of the tile they enter.
+template <int NBT, bool HE, bool HEAT>
+__global__ void __launch_bounds__(kTileBlock, 1) k_tile_pass(StepArgs a, BinTables t, WFArgs w,
+                                                             const unsigned* boff, const unsigned* list,
+                                                             const unsigned* nlist, unsigned* next,
+                                                             int64_t n_keys) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* sabs = reinterpret_cast<float4*>(smem);
+  unsigned long long* sdep = reinterpret_cast<unsigned long long*>(smem + 4096 * sizeof(float4));
+  __shared__ unsigned s_item;
+  const int nb = NBT > 0 ? NBT : t.n_bins;
+  const unsigned ntl = *nlist;
+  const float4* abs32 = reinterpret_cast<const float4*>(a.abs32);
+  Tally tl{0, 0, 0, 0u, 0u};
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1u);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= ntl) break;
+    const unsigned T = list[item];
+    const int b = box_of_tile(a.boxes, a.n_boxes, T);
+    const BoxMeta* M = a.boxes + b;
+    const unsigned lt = T - (unsigned)(M->tile_off >> 3);
+    const int x0 = 16 * (int)compact3(lt), y0 = 16 * (int)compact3(lt >> 1), z0 = 16 * (int)compact3(lt >> 2);
+    const int ex = min(16, M->nx - x0), ey = min(16, M->ny - y0), ez = min(16, M->nz - z0);
+    const unsigned lo = boff[8 * (int64_t)T], hi = tile_end(boff, w.count_in, n_keys, T);
+    const bool dense = (hi - lo) >= (unsigned)kTileMinPackets;
+    if (dense) {
+      for (int li = threadIdx.x; li < 4096; li += blockDim.x) {
+        const int lx = li & 15, ly = (li >> 4) & 15, lz = li >> 8;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lx < ex && ly < ey && lz < ez)
+          v = __ldg(abs32 + M->cell_off + (x0 + lx) + M->nx * ((y0 + ly) + M->ny * (z0 + lz)));
+        sabs[li] = v;
+        reinterpret_cast<ulonglong2*>(sdep)[2 * li] = make_ulonglong2(0ull, 0ull);
+        reinterpret_cast<ulonglong2*>(sdep)[2 * li + 1] = make_ulonglong2(0ull, 0ull);
+      }
+    }
+    __syncthreads();
+    for (unsigned base = lo; base < hi; base += blockDim.x) {
+      const unsigned j = base + threadIdx.x;
+      int pb = -1;
+      bool alive = false;
+      int ix = 0, iy = 0, iz = 0;
+      float tMx = 0.f, tMy = 0.f, tMz = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+      long long N[NBT > 0 ? NBT : CRASH_MAX_BINS];
+      if (j < hi) {
+        load_record<NBT>(w.rec_in, w.rs, (long long)w.perm[j], ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz,
+                         N, nb);
+        int r;
+        if (dense) {
+          TileCells cells{sabs, sdep, x0, y0, z0};
+          r = walk<NBT, HE, HEAT, true>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells, t, nb, 64, tl,
+                                        x0, y0, z0, ex, ey, ez);
+        } else {
+          GlobalCells cells{abs32, a.dep, M->cell_off, M->nx, M->ny};
+          r = walk<NBT, HE, HEAT, true>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells, t, nb, 64, tl,
+                                        x0, y0, z0, ex, ey, ez);
+        }
+        if (r == ESCAPED) {
+          for (int jj = 0; jj < nb; ++jj) tl.escaped += (unsigned long long)N[jj];
+        }
+        alive = (r == ALIVE);
+      }
+      write_survivor<NBT>(a, w, alive, ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz, N, nb);
+      flush_warp(a, pb, tl);
+    }
+    __syncthreads();
+    if (dense) {
+      for (int li = threadIdx.x; li < 4096; li += blockDim.x) {
+        const int lx = li & 15, ly = (li >> 4) & 15, lz = li >> 8;
+        if (lx < ex && ly < ey && lz < ez) {
+          const int64_t cell = M->cell_off + (x0 + lx) + M->nx * ((y0 + ly) + M->ny * (z0 + lz));
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const unsigned long long v = sdep[4 * li + k];
+            if (v) atomicAdd(a.dep + 4 * cell + k, v);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_check_drained(const unsigned* count, int* err) {
   if (*count != 0u) atomicOr(err, ERR_WATCHDOG);
 }
 
-WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys) {
+WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys, int tile = 0) {
   WFArgs w;
+  w.tile = tile;
   const int out = 1 - in;
   w.rec_in = wf->rec[in];
   w.rec_out = wf->rec[out];
@@ -587,6 +793,54 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
                                                                        max_iter, max_iter);
     toc();
     return 1;
+  }
+  if (o.tile && wf->tiles) {
+    // emission only (no walk), then tile passes until every packet is done
+    static bool smem_set = false;
+    if (!smem_set) {
+      cudaFuncSetAttribute(k_tile_pass<NBT, HE, HEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTileSmem);
+      smem_set = true;
+    }
+    const int64_t nk = a.n_tile_keys;
+    const int nscan_t = (int)((nk + 4095) / 4096);
+    for (int64_t g0 = 0; g0 < a.total_packets; g0 += wf->cap) {
+      const int64_t n = std::min<int64_t>(wf->cap, a.total_packets - g0);
+      int cur = 1;
+      cudaMemsetAsync(wf->count, 0, 4 * sizeof(unsigned), s);
+      cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * nk, s);
+      {
+        WFArgs w = wf_args(wf, cur, false, true, 1);
+        int64_t blocks = (n + block - 1) / block;
+        if (blocks > persistent * 4) blocks = persistent * 4;
+        tic();
+        k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
+        toc();
+        ++launches;
+        cur = 0;
+      }
+      for (int p = 1; p <= a.max_tiles; ++p) {
+        k_scan_blocks<<<nscan_t, 1024, 0, s>>>(wf->bcount, wf->boff, wf->bsum, nk);
+        k_scan_sums<<<1, 1024, 0, s>>>(wf->bsum, nscan_t);
+        k_scan_add<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(wf->boff, wf->bsum, nk);
+        k_perm<<<persistent, block, 0, s>>>(wf->count + cur, wf->key, wf->rank, wf->boff, wf->perm, a.err);
+        cudaMemsetAsync(wf->count + 2, 0, 2 * sizeof(unsigned), s);
+        k_tile_list<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nk / 8 + 255) / 256, 4096)), 256, 0, s>>>(
+            wf->boff, wf->count + cur, nk, wf->tiles, wf->count + 2);
+        cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * nk, s);
+        WFArgs w = wf_args(wf, cur, true, true, 1);
+        cudaMemsetAsync(w.count_out, 0, sizeof(unsigned), s);
+        tic();
+        k_tile_pass<NBT, HE, HEAT><<<num_sms(), kTileBlock, kTileSmem, s>>>(
+            a, t, w, wf->boff, wf->tiles, wf->count + 2, wf->count + 3, nk);
+        toc();
+        launches += 6;
+        cur = 1 - cur;
+      }
+      k_check_drained<<<1, 1, 0, s>>>(wf->count + cur, a.err);
+      ++launches;
+    }
+    return launches;
   }
   const int S = o.seg_per_iter > 0 ? o.seg_per_iter : 32;
   const int R = o.resort_interval == 0 ? 1 : o.resort_interval;
@@ -672,6 +926,7 @@ int launch_trace_mixed_external(const StepArgs& a, const BinTables& t, const cra
   crash_run_opts oo = o;
   oo.wavefront = 1;
   oo.resort_interval = -1;     // no sort keys without their workspace
+  oo.tile = 0;
   return launch_trace_mixed(a, t, oo, &wf, max_iter, s, nullptr, nullptr);
 }
 
@@ -690,6 +945,7 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
     if (e == cudaSuccess) e = cudaMalloc(&w->bcount, sizeof(unsigned) * n_keys);
     if (e == cudaSuccess) e = cudaMalloc(&w->boff, sizeof(unsigned) * n_keys);
     if (e == cudaSuccess) e = cudaMalloc(&w->bsum, sizeof(unsigned) * 1024);
+    if (e == cudaSuccess) e = cudaMalloc(&w->tiles, sizeof(unsigned) * (n_keys / 8 + 1));
   }
   if (err) *err = e;
   if (e != cudaSuccess) {
@@ -702,7 +958,7 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
 void wavefront_destroy(void* p) {
   WF* w = (WF*)p;
   if (!w) return;
-  void* ptrs[] = {w->count, w->key, w->rank, w->perm, w->bcount, w->boff, w->bsum,
+  void* ptrs[] = {w->count, w->key, w->rank, w->perm, w->bcount, w->boff, w->bsum, w->tiles,
                   w->rec[0], w->rec[1]};
   for (void* q : ptrs)
     if (q) cudaFree(q);

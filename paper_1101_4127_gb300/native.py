@@ -52,7 +52,7 @@ class crash_run_opts(C.Structure):
                 ("chem_eps", C.c_double), ("chem_max_sub", C.c_int), ("cool_mask", C.c_int),
                 ("block_size", C.c_int), ("seg_per_iter", C.c_int), ("resort_interval", C.c_int),
                 ("wavefront", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
-                ("reg_cap", C.c_int)]
+                ("reg_cap", C.c_int), ("tile", C.c_int)]
 
 
 def library_path() -> str:
@@ -94,7 +94,8 @@ def lib(build_if_missing: bool = True):
             L.crash_launch_count.argtypes = [P]
             L.crash_launch_count.restype = C.c_int64
             L.crash_autotune.argtypes = [P, C.c_double, C.POINTER(C.c_uint64), C.POINTER(C.c_int),
-                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int)]
             L.crash_transport_noalloc.argtypes = [
                 C.POINTER(crash_grid_desc), C.c_int, dp, dp, C.c_int, dp, dp, C.c_double, C.c_uint64,
                 C.c_uint64, C.c_int, P, P, C.POINTER(C.c_int64), P]
@@ -235,10 +236,10 @@ class Grid:
 
     def autotune(self, dt_s, packets):
         arr = (C.c_uint64 * len(packets))(*[int(p) for p in packets])
-        bs, sg, rs, rc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        bs, sg, rs, rc, tl = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
         self._check(self.L.crash_autotune(self.ctx, float(dt_s), arr, C.byref(bs), C.byref(sg),
-                                          C.byref(rs), C.byref(rc)))
-        return bs.value, sg.value, rs.value, rc.value
+                                          C.byref(rs), C.byref(rc), C.byref(tl)))
+        return bs.value, sg.value, rs.value, rc.value, tl.value
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -37,10 +37,24 @@ def test_mixed_budget_closes_and_launch_shapes_agree_bit_for_bit():
     dt = 0.01 * inputs.MYR_S
     ref = _fields(_run(box, P, 2, dt, wavefront=0))
     assert ref[-1][0] == ref[-1][1] + ref[-1][2]
-    for S, R in [(1, -1), (7, 1), (16, 2), (64, 3), (5, 1)]:
-        got = _fields(_run(box, P, 2, dt, wavefront=1, seg_per_iter=S, resort_interval=R))
+    for S, R, cap in [(1, -1, 0), (7, 1, 1), (16, 2, 0), (64, 3, 1), (5, 1, 0)]:
+        got = _fields(_run(box, P, 2, dt, wavefront=1, seg_per_iter=S, resort_interval=R, reg_cap=cap))
         for a, b in zip(ref, got):
-            assert np.array_equal(a, b), (S, R)
+            assert np.array_equal(a, b), (S, R, cap)
+    got = _fields(_run(box, P, 2, dt, wavefront=1, tile=1))      # shared-memory tile passes
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b), "tile"
+
+
+def test_tile_passes_dense_tiles_bit_for_bit():
+    """Enough packets per 16^3 tile that the tiles are staged in shared memory."""
+    box = small_hhe_box((40, 36, 20), n_src=3, seed=140)
+    P = 3 * 60000
+    dt = 0.01 * inputs.MYR_S
+    ref = _fields(_run(box, P, 2, dt, wavefront=0))
+    got = _fields(_run(box, P, 2, dt, wavefront=1, tile=1))
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
 
 
 def test_mixed_graph_replay_identical():
