@@ -48,7 +48,7 @@ struct WF {
   unsigned* bcount = nullptr;            // [n_keys]
   unsigned* boff = nullptr;              // [n_keys]
   unsigned* bsum = nullptr;              // [1024]
-  unsigned* tiles = nullptr;             // [n_keys / 8] non-empty tiles of a tile pass
+  uint2* items = nullptr;                // work items of a tile pass (tile, first position)
   int64_t n_keys = 0;
 };
 
@@ -171,7 +171,7 @@ __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 
     if (HE) {
       k1 = tHeI * t.sigma32[1][j];
       k2 = tHeII * t.sigma32[2][j];
-      tau = (k0 + k1) + k2;
+      tau = fmaf(tHeII, t.sigma32[2][j], fmaf(tHeI, t.sigma32[1][j], k0));
     }
     long long Nj = N[j];
     if (tau > 0.f && Nj > 0) {
@@ -219,7 +219,7 @@ struct GlobalCells {
   __device__ __forceinline__ int64_t index(int ix, int iy, int iz) const {
     return coff + (ix + nx * (iy + ny * iz));
   }
-  __device__ __forceinline__ float4 load(int64_t c) const { return __ldg(abs + c); }
+  __device__ __forceinline__ float4 load(int64_t c, int, int, int) const { return __ldg(abs + c); }
   __device__ __forceinline__ void add(int64_t c, long long a0, long long a1, long long a2, long long e) const {
     unsigned long long* dp = dep + 4 * c;
     if (a0) atomicAdd(dp + 0, (unsigned long long)a0);
@@ -229,16 +229,19 @@ struct GlobalCells {
   }
 };
 
-// ... or one 16^3-cell tile staged in shared memory (absorbers copied in,
-// deposits accumulated with shared atomics and flushed once per tile visit)
+// ... or one 16^3-cell tile whose absorbers are staged in shared memory
+// (deposits still go to the grid: they stay in L2 while the tile is worked)
 struct TileCells {
-  const float4* abs;               // shared, [16][16][16]
-  unsigned long long* dep;         // shared, [16][16][16][4]
-  int x0, y0, z0;
+  const float4* sabs;              // shared, [16][16][16]
+  unsigned long long* dep;
+  int64_t coff;
+  int nx, ny, x0, y0, z0;
   __device__ __forceinline__ int64_t index(int ix, int iy, int iz) const {
-    return (ix - x0) + 16 * ((iy - y0) + 16 * (iz - z0));
+    return coff + (ix + nx * (iy + ny * iz));
   }
-  __device__ __forceinline__ float4 load(int64_t c) const { return abs[c]; }
+  __device__ __forceinline__ float4 load(int64_t, int ix, int iy, int iz) const {
+    return sabs[(ix - x0) + 16 * ((iy - y0) + 16 * (iz - z0))];
+  }
   __device__ __forceinline__ void add(int64_t c, long long a0, long long a1, long long a2, long long e) const {
     unsigned long long* dp = dep + 4 * c;
     if (a0) atomicAdd(dp + 0, (unsigned long long)a0);
@@ -273,7 +276,7 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
   float seg = fminf(tMx, fminf(tMy, tMz));
   int ax = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
   int64_t cell = cells.index(ix, iy, iz);
-  float4 ab = cells.load(cell);
+  float4 ab = cells.load(cell, ix, iy, iz);
   for (int it = 1;; ++it) {
     // step the walk into the next cell and request its absorbers
     tMx -= seg;
@@ -298,7 +301,7 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
       seg_n = fminf(tMx, fminf(tMy, tMz));
       ax_n = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
       cell_n = cells.index(ix, iy, iz);
-      ab_n = cells.load(cell_n);
+      ab_n = cells.load(cell_n, ix, iy, iz);
     }
     // attenuate and deposit in the current cell
     if (seg > 0.f) {
@@ -596,9 +599,9 @@ __global__ void k_perm(const unsigned* count, const unsigned* key, const unsigne
 }
 
 // ------------------------------------------------------------------ tiles
-constexpr int kTileMinPackets = 256;   // sparser tiles walk over global memory
-constexpr int kTileBlock = 512;
-constexpr size_t kTileSmem = 4096 * sizeof(float4) + 4096 * 4 * sizeof(unsigned long long);
+constexpr int kTileItem = 2048;        // packets of a tile handled by one block visit
+constexpr int kTileBlock = 256;
+constexpr size_t kTileSmem = 4096 * sizeof(float4);
 
 __device__ __forceinline__ unsigned compact3(unsigned v) {   // every third bit -> 10 bits
   v &= 0x09249249u;
@@ -624,60 +627,61 @@ __device__ __forceinline__ unsigned tile_end(const unsigned* boff, const unsigne
   return (8 * (int64_t)T + 8 < n_keys) ? boff[8 * (int64_t)T + 8] : *count;
 }
 
-// list of the tiles that hold packets (any order: results do not depend on it)
-__global__ void k_tile_list(const unsigned* boff, const unsigned* count, int64_t n_keys, unsigned* list,
-                            unsigned* nlist) {
+// work items of a tile pass: (tile, first sorted position), at most
+// kTileItem packets each, in any order (results do not depend on it)
+__global__ void k_tile_list(const unsigned* boff, const unsigned* count, int64_t n_keys, uint2* items,
+                            unsigned* nitems) {
   const int64_t ntiles = n_keys / 8;
   for (int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; T < ntiles;
        T += (int64_t)gridDim.x * blockDim.x) {
-    if (tile_end(boff, count, n_keys, (unsigned)T) > boff[8 * T]) list[atomicAdd(nlist, 1u)] = (unsigned)T;
+    const unsigned lo = boff[8 * T], hi = tile_end(boff, count, n_keys, (unsigned)T);
+    if (hi > lo) {
+      const unsigned k = (hi - lo + kTileItem - 1) / kTileItem;
+      const unsigned at = atomicAdd(nitems, k);
+      for (unsigned q = 0; q < k; ++q) items[at + q] = make_uint2((unsigned)T, lo + q * kTileItem);
+    }
   }
 }
 
-// One tile pass: a block takes the next non-empty tile, copies its 16^3
-// absorbers into shared memory, walks every packet of the tile until it
-// leaves the tile (or is absorbed or escapes), accumulating the deposits in
-// shared memory, then adds them to the grid once.  Tiles with few packets
-// are walked over global memory instead.  Survivors go to the output queue
-// with the key of the tile they enter.
+// One tile pass: a block takes the next work item, copies the tile's 16^3
+// absorbers into shared memory and walks each of the item's packets until it
+// leaves the tile (or is absorbed or escapes); deposits go to the grid.
+// Survivors go to the output queue with the key of the tile they enter.
 template <int NBT, bool HE, bool HEAT>
-__global__ void __launch_bounds__(kTileBlock, 1) k_tile_pass(StepArgs a, BinTables t, WFArgs w,
-                                                             const unsigned* boff, const unsigned* list,
-                                                             const unsigned* nlist, unsigned* next,
+__global__ void __launch_bounds__(kTileBlock, 3) k_tile_pass(StepArgs a, BinTables t, WFArgs w,
+                                                             const unsigned* boff, const uint2* items,
+                                                             const unsigned* nitems, unsigned* next,
                                                              int64_t n_keys) {
   extern __shared__ __align__(16) unsigned char smem[];
   float4* sabs = reinterpret_cast<float4*>(smem);
-  unsigned long long* sdep = reinterpret_cast<unsigned long long*>(smem + 4096 * sizeof(float4));
   __shared__ unsigned s_item;
   const int nb = NBT > 0 ? NBT : t.n_bins;
-  const unsigned ntl = *nlist;
+  const unsigned nit = *nitems;
   const float4* abs32 = reinterpret_cast<const float4*>(a.abs32);
   Tally tl{0, 0, 0, 0u, 0u};
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next, 1u);
     __syncthreads();
     const unsigned item = s_item;
-    if (item >= ntl) break;
-    const unsigned T = list[item];
+    if (item >= nit) break;
+    const uint2 it = items[item];
+    const unsigned T = it.x;
     const int b = box_of_tile(a.boxes, a.n_boxes, T);
     const BoxMeta* M = a.boxes + b;
     const unsigned lt = T - (unsigned)(M->tile_off >> 3);
     const int x0 = 16 * (int)compact3(lt), y0 = 16 * (int)compact3(lt >> 1), z0 = 16 * (int)compact3(lt >> 2);
     const int ex = min(16, M->nx - x0), ey = min(16, M->ny - y0), ez = min(16, M->nz - z0);
-    const unsigned lo = boff[8 * (int64_t)T], hi = tile_end(boff, w.count_in, n_keys, T);
-    const bool dense = (hi - lo) >= (unsigned)kTileMinPackets;
-    if (dense) {
-      for (int li = threadIdx.x; li < 4096; li += blockDim.x) {
-        const int lx = li & 15, ly = (li >> 4) & 15, lz = li >> 8;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lx < ex && ly < ey && lz < ez)
-          v = __ldg(abs32 + M->cell_off + (x0 + lx) + M->nx * ((y0 + ly) + M->ny * (z0 + lz)));
-        sabs[li] = v;
-        reinterpret_cast<ulonglong2*>(sdep)[2 * li] = make_ulonglong2(0ull, 0ull);
-        reinterpret_cast<ulonglong2*>(sdep)[2 * li + 1] = make_ulonglong2(0ull, 0ull);
-      }
+    const unsigned lo = it.y;
+    const unsigned hi = min(lo + (unsigned)kTileItem, tile_end(boff, w.count_in, n_keys, T));
+    for (int li = threadIdx.x; li < 4096; li += blockDim.x) {
+      const int lx = li & 15, ly = (li >> 4) & 15, lz = li >> 8;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lx < ex && ly < ey && lz < ez)
+        v = __ldg(abs32 + M->cell_off + (x0 + lx) + M->nx * ((y0 + ly) + M->ny * (z0 + lz)));
+      sabs[li] = v;
     }
     __syncthreads();
+    const TileCells cells{sabs, a.dep, M->cell_off, M->nx, M->ny, x0, y0, z0};
     for (unsigned base = lo; base < hi; base += blockDim.x) {
       const unsigned j = base + threadIdx.x;
       int pb = -1;
@@ -688,16 +692,8 @@ __global__ void __launch_bounds__(kTileBlock, 1) k_tile_pass(StepArgs a, BinTabl
       if (j < hi) {
         load_record<NBT>(w.rec_in, w.rs, (long long)w.perm[j], ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz,
                          N, nb);
-        int r;
-        if (dense) {
-          TileCells cells{sabs, sdep, x0, y0, z0};
-          r = walk<NBT, HE, HEAT, true>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells, t, nb, 64, tl,
-                                        x0, y0, z0, ex, ey, ez);
-        } else {
-          GlobalCells cells{abs32, a.dep, M->cell_off, M->nx, M->ny};
-          r = walk<NBT, HE, HEAT, true>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells, t, nb, 64, tl,
-                                        x0, y0, z0, ex, ey, ez);
-        }
+        const int r = walk<NBT, HE, HEAT, true>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells, t, nb,
+                                                64, tl, x0, y0, z0, ex, ey, ez);
         if (r == ESCAPED) {
           for (int jj = 0; jj < nb; ++jj) tl.escaped += (unsigned long long)N[jj];
         }
@@ -705,20 +701,6 @@ __global__ void __launch_bounds__(kTileBlock, 1) k_tile_pass(StepArgs a, BinTabl
       }
       write_survivor<NBT>(a, w, alive, ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz, N, nb);
       flush_warp(a, pb, tl);
-    }
-    __syncthreads();
-    if (dense) {
-      for (int li = threadIdx.x; li < 4096; li += blockDim.x) {
-        const int lx = li & 15, ly = (li >> 4) & 15, lz = li >> 8;
-        if (lx < ex && ly < ey && lz < ez) {
-          const int64_t cell = M->cell_off + (x0 + lx) + M->nx * ((y0 + ly) + M->ny * (z0 + lz));
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const unsigned long long v = sdep[4 * li + k];
-            if (v) atomicAdd(a.dep + 4 * cell + k, v);
-          }
-        }
-      }
     }
     __syncthreads();
   }
@@ -794,7 +776,7 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
     toc();
     return 1;
   }
-  if (o.tile && wf->tiles) {
+  if (o.tile && wf->items) {
     // emission only (no walk), then tile passes until every packet is done
     static bool smem_set = false;
     if (!smem_set) {
@@ -826,13 +808,13 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
         k_perm<<<persistent, block, 0, s>>>(wf->count + cur, wf->key, wf->rank, wf->boff, wf->perm, a.err);
         cudaMemsetAsync(wf->count + 2, 0, 2 * sizeof(unsigned), s);
         k_tile_list<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nk / 8 + 255) / 256, 4096)), 256, 0, s>>>(
-            wf->boff, wf->count + cur, nk, wf->tiles, wf->count + 2);
+            wf->boff, wf->count + cur, nk, wf->items, wf->count + 2);
         cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * nk, s);
         WFArgs w = wf_args(wf, cur, true, true, 1);
         cudaMemsetAsync(w.count_out, 0, sizeof(unsigned), s);
         tic();
-        k_tile_pass<NBT, HE, HEAT><<<num_sms(), kTileBlock, kTileSmem, s>>>(
-            a, t, w, wf->boff, wf->tiles, wf->count + 2, wf->count + 3, nk);
+        k_tile_pass<NBT, HE, HEAT><<<num_sms() * 3, kTileBlock, kTileSmem, s>>>(
+            a, t, w, wf->boff, wf->items, wf->count + 2, wf->count + 3, nk);
         toc();
         launches += 6;
         cur = 1 - cur;
@@ -945,7 +927,7 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
     if (e == cudaSuccess) e = cudaMalloc(&w->bcount, sizeof(unsigned) * n_keys);
     if (e == cudaSuccess) e = cudaMalloc(&w->boff, sizeof(unsigned) * n_keys);
     if (e == cudaSuccess) e = cudaMalloc(&w->bsum, sizeof(unsigned) * 1024);
-    if (e == cudaSuccess) e = cudaMalloc(&w->tiles, sizeof(unsigned) * (n_keys / 8 + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&w->items, sizeof(uint2) * (n_keys / 8 + cap / 2048 + 2));
   }
   if (err) *err = e;
   if (e != cudaSuccess) {
@@ -958,7 +940,7 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
 void wavefront_destroy(void* p) {
   WF* w = (WF*)p;
   if (!w) return;
-  void* ptrs[] = {w->count, w->key, w->rank, w->perm, w->bcount, w->boff, w->bsum, w->tiles,
+  void* ptrs[] = {w->count, w->key, w->rank, w->perm, w->bcount, w->boff, w->bsum, w->items,
                   w->rec[0], w->rec[1]};
   for (void* q : ptrs)
     if (q) cudaFree(q);
