@@ -267,6 +267,10 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
   c->n_tile_keys = tkeys;
   auto fail = [&](crash_status st) { release(c); return st; };
   if (c->precision == CRASH_MIXED) {
+    if (n_boxes > 2048) {
+      g_create_error = "mixed form: at most 2048 boxes per batch";
+      return fail(CRASH_ERR_OVERFLOW);
+    }
     for (int i = 0; i < n_boxes; ++i)
       if (descs[i].nx > 65535 || descs[i].ny > 65535 || descs[i].nz > 65535 ||
           (int64_t)descs[i].nx * descs[i].ny * descs[i].nz >= ((int64_t)1 << 31)) {

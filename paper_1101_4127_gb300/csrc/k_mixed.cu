@@ -30,12 +30,8 @@ using namespace crash;
 
 namespace {
 
-// Packet records (array of structures, one per packet, RS bytes):
-//   [0,16)  float4 (tMx, tMy, tMz, dx)   distances to the next faces, x direction
-//   [16,24) uint2  (ix | iy << 16, iz | box << 16)
-//   [24,32) float2 (dy, dz)
-//   [32, )  int64  N[n_bins]             photon content per bin
-// RS = 32 + 8 n_bins rounded up to 16 bytes (96 for 8 bins).
+// Packet records: array of structures, one record per packet (layout at
+// store_record).
 struct WF {
   int64_t cap = 0;
   int nb = 0;
@@ -99,14 +95,8 @@ __device__ __forceinline__ void flush_warp(const StepArgs& a, int b, Tally& t) {
   t = Tally{0, 0, 0, 0u, 0u};
 }
 
-// int64 <-> FP32 conversions without the hardware 64-bit conversions, which
-// on this GPU issue to the narrow FP64 pipe.  N in [0, 2^63) to FP32 from its
-// two 32-bit halves (relative error below 2^-23).
-__device__ __forceinline__ float ll_to_float(long long N) {
-  const unsigned long long u = (unsigned long long)N;
-  return fmaf(__uint2float_rn((unsigned)(u >> 32)), 4294967296.0f, __uint2float_rn((unsigned)u));
-}
-
+// FP32 <-> integer conversions without the hardware 64-bit conversions,
+// which on this GPU issue to the narrow FP64 pipe.
 // rint(x) for x in [0, 2^63), round half to even
 __device__ __forceinline__ long long float_to_ll(float x) {
   if (x < 8388608.0f)   // below 2^23 adding 2^23 rounds to an integer in the last place
@@ -130,37 +120,58 @@ __device__ __forceinline__ float absorbed_over_tau(float tau) {
   return p;
 }
 
-// Absorbed count of one bin: for tau < 0.5 round N (1 - e^-tau), else round
-// the transmitted N e^-tau and take the difference, so that the smaller of
-// the two parts always carries ~1e-7 relative error.  q is the absorbed
-// count divided by tau in FP32: the species share of species s is q k_s.
-__device__ __forceinline__ long long absorb(long long N, float tau, float& q) {
-  const float Nf = ll_to_float(N);
+// rint(x) for x in [0, 2^32), round half to even
+__device__ __forceinline__ unsigned float_to_u32(float x) {
+  if (x < 8388608.0f) return __float_as_uint(x + 8388608.0f) - 0x4B000000u;
+  return __float2uint_rn(x);
+}
+
+// Absorbed count of one bin of content m (in the packet's units): for
+// tau < 0.5 round m (1 - e^-tau), else round the transmitted m e^-tau and
+// take the difference, so that the smaller of the two parts always carries
+// ~1e-7 relative error.  q is the absorbed count divided by tau in FP32: the
+// share of species s is q k_s.
+__device__ __forceinline__ unsigned absorb(unsigned m, float tau, float& q) {
+  const float Nf = __uint2float_rn(m);
   if (tau < 0.5f) {
     q = Nf * absorbed_over_tau(tau);
-    const long long A = float_to_ll(q * tau);
-    return A > N ? N : A;
+    const unsigned A = float_to_u32(q * tau);
+    return A > m ? m : A;
   }
   const float T = Nf * expf(-tau);
   q = (Nf - T) * __fdividef(1.0f, tau);
-  long long Np = float_to_ll(T);
-  Np = Np > N ? N : Np;
-  return N - Np;
+  unsigned Np = float_to_u32(T);
+  Np = Np > m ? m : Np;
+  return m - Np;
 }
+
+// Packet content: per bin a 32-bit count m_j in units of 2^e photon quanta
+// (e >= 0 is the packet's exponent), so N_j = m_j 2^e exactly.
+template <int NBT>
+struct Content {
+  unsigned m[NBT > 0 ? NBT : CRASH_MAX_BINS];
+  int e;
+  __device__ __forceinline__ unsigned long long total(int nb) const {
+    unsigned long long t = 0;
+    for (int j = 0; j < nb; ++j) t += m[j];
+    return t << e;
+  }
+};
 
 enum { ALIVE = 0, ABSORBED = 1, ESCAPED = 2 };
 
 // Attenuation and deposition in one crossed cell (Sec. 2, Eq. 1) for a
-// segment of seg cells: updates the packet's bins N and returns the absorbed
-// total; the species and heating deposits of the cell come back in d*.
+// segment of seg cells: updates the packet's bins and returns the absorbed
+// total in photon quanta; the species and heating deposits of the cell come
+// back in d* (quanta), left is nonzero while some bin holds photons.
 template <int NBT, bool HE, bool HEAT>
-__device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 ab, long long* N,
+__device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 ab, Content<NBT>& c,
                                                     int nb, const BinTables& t, long long& dHI,
                                                     long long& dHeI, long long& dHeII, long long& dE,
-                                                    long long& left) {
+                                                    unsigned& left) {
   const float l = seg * dl;
   const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
-  long long Atot = 0;
+  unsigned long long At = 0;
   left = 0;
   float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
 #pragma unroll
@@ -173,13 +184,13 @@ __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 
       k2 = tHeII * t.sigma32[2][j];
       tau = fmaf(tHeII, t.sigma32[2][j], fmaf(tHeI, t.sigma32[1][j], k0));
     }
-    long long Nj = N[j];
-    if (tau > 0.f && Nj > 0) {
+    unsigned mj = c.m[j];
+    if (tau > 0.f && mj > 0u) {
       float q;
-      const long long A = absorb(Nj, tau, q);
-      Nj -= A;
-      N[j] = Nj;
-      Atot += A;
+      const unsigned A = absorb(mj, tau, q);
+      mj -= A;
+      c.m[j] = mj;
+      At += A;
       if (HE) {
         fHeI = fmaf(q, k1, fHeI);
         fHeII = fmaf(q, k2, fHeII);
@@ -191,22 +202,26 @@ __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 
           fheat = fmaf(q * k0, t.wheat32[0][j], fheat);
       }
     }
-    left |= Nj;
+    left |= mj;
   }
-  dHeI = 0;
-  dHeII = 0;
-  dE = 0;
-  if (Atot) {
+  // species split and heating rounded once per cell in the packet's units,
+  // then scaled to photon quanta
+  long long a1 = 0, a2 = 0, h = 0;
+  const long long Au = (long long)At;
+  if (At) {
     if (HE) {
-      dHeI = float_to_ll(fHeI);
-      dHeI = dHeI > Atot ? Atot : dHeI;
-      dHeII = float_to_ll(fHeII);
-      dHeII = dHeII > Atot - dHeI ? Atot - dHeI : dHeII;
+      a1 = float_to_ll(fHeI);
+      a1 = a1 > Au ? Au : a1;
+      a2 = float_to_ll(fHeII);
+      a2 = a2 > Au - a1 ? Au - a1 : a2;
     }
-    if (HEAT) dE = float_to_ll(fheat);
+    if (HEAT) h = float_to_ll(fheat);
   }
-  dHI = Atot - dHeI - dHeII;
-  return Atot;
+  dHeI = a1 << c.e;
+  dHeII = a2 << c.e;
+  dHI = (Au - a1 - a2) << c.e;
+  dE = h << c.e;
+  return Au << c.e;
 }
 
 // Where a walk reads absorbers and adds deposits: the grid in global memory
@@ -260,7 +275,7 @@ struct TileCells {
 // also stops (alive) when it steps out of the box [tx0,tx0+ex) x ... .
 template <int NBT, bool HE, bool HEAT, bool TILE, class Cells>
 __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float& tMy, float& tMz,
-                                    const float dx, const float dy, const float dz, long long* N,
+                                    const float dx, const float dy, const float dz, Content<NBT>& N,
                                     const BoxMeta* M, const Cells& cells, const BinTables& t,
                                     const int nb, const int max_iter, Tally& tl, int tx0 = 0,
                                     int ty0 = 0, int tz0 = 0, int ex = 0, int ey = 0, int ez = 0) {
@@ -305,7 +320,8 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
     }
     // attenuate and deposit in the current cell
     if (seg > 0.f) {
-      long long dHI, dHeI, dHeII, dE, left;
+      long long dHI, dHeI, dHeII, dE;
+      unsigned left;
       const long long Atot = cell_attenuate<NBT, HE, HEAT>(seg, dl, ab, N, nb, t, dHI, dHeI, dHeII,
                                                            dE, left);
       if (Atot) {
@@ -329,7 +345,7 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
 template <int NBT, bool HE, bool HEAT>
 __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx, float& tMy,
                                            float& tMz, const float dx, const float dy,
-                                           const float dz, long long* N, const BoxMeta* M,
+                                           const float dz, Content<NBT>& N, const BoxMeta* M,
                                            const StepArgs& a, const BinTables& t, const int nb,
                                            const int max_iter, Tally& tl) {
   GlobalCells cells{reinterpret_cast<const float4*>(a.abs32), a.dep, M->cell_off, M->nx, M->ny};
@@ -372,41 +388,56 @@ __device__ __forceinline__ unsigned sort_key(const BoxMeta* boxes, int box, int 
   return base + ((mort << 3) | oct);
 }
 
+// Packet records, RS bytes each (RS = 32 + 4 n_bins rounded up to 16 bytes,
+// 64 for 8 bins):
+//   [0,16)  float4 (tMx, tMy, tMz, dx)
+//   [16,32) uint4  (ix | iy << 16, iz | box << 16 | e << 27, dy, dz)
+//   [32, )  uint32 m[n_bins]
 template <int NBT>
 __device__ __forceinline__ void store_record(char* rec, int rs, long long slot, int ix, int iy, int iz,
                                              int box, float tMx, float tMy, float tMz, float dx,
-                                             float dy, float dz, const long long* N, int nb) {
+                                             float dy, float dz, const Content<NBT>& c, int nb) {
   char* r = rec + (int64_t)rs * slot;
   *reinterpret_cast<float4*>(r) = make_float4(tMx, tMy, tMz, dx);
   *reinterpret_cast<uint4*>(r + 16) =
-      make_uint4((unsigned)ix | ((unsigned)iy << 16), (unsigned)iz | ((unsigned)box << 16),
+      make_uint4((unsigned)ix | ((unsigned)iy << 16),
+                 (unsigned)iz | ((unsigned)box << 16) | ((unsigned)c.e << 27),
                  __float_as_uint(dy), __float_as_uint(dz));
-  longlong2* n2 = reinterpret_cast<longlong2*>(r + 32);
+  uint4* m4 = reinterpret_cast<uint4*>(r + 32);
 #pragma unroll
-  for (int j = 0; j < (NBT > 0 ? (NBT + 1) / 2 : CRASH_MAX_BINS / 2); ++j) {
-    if (NBT == 0 && 2 * j >= nb) break;
-    n2[j] = make_longlong2(N[2 * j], (2 * j + 1 < nb) ? N[2 * j + 1] : 0ll);
+  for (int j = 0; j < (NBT > 0 ? (NBT + 3) / 4 : CRASH_MAX_BINS / 4); ++j) {
+    if (NBT == 0 && 4 * j >= nb) break;
+    const int k = 4 * j;
+    const int lim = NBT > 0 ? NBT : CRASH_MAX_BINS;
+    m4[j] = make_uint4(c.m[k], (k + 1 < lim && k + 1 < nb) ? c.m[k + 1] : 0u,
+                       (k + 2 < lim && k + 2 < nb) ? c.m[k + 2] : 0u,
+                       (k + 3 < lim && k + 3 < nb) ? c.m[k + 3] : 0u);
   }
 }
 
 template <int NBT>
 __device__ __forceinline__ void load_record(const char* rec, int rs, long long i, int& ix, int& iy,
                                             int& iz, int& box, float& tMx, float& tMy, float& tMz,
-                                            float& dx, float& dy, float& dz, long long* N, int nb) {
+                                            float& dx, float& dy, float& dz, Content<NBT>& c, int nb) {
   const char* r = rec + (int64_t)rs * i;
   const float4 td = *reinterpret_cast<const float4*>(r);
   const uint4 cd = *reinterpret_cast<const uint4*>(r + 16);
   tMx = td.x; tMy = td.y; tMz = td.z; dx = td.w;
   ix = (int)(cd.x & 0xFFFFu); iy = (int)(cd.x >> 16);
-  iz = (int)(cd.y & 0xFFFFu); box = (int)(cd.y >> 16);
+  iz = (int)(cd.y & 0xFFFFu); box = (int)((cd.y >> 16) & 0x7FFu);
+  c.e = (int)(cd.y >> 27);
   dy = __uint_as_float(cd.z); dz = __uint_as_float(cd.w);
-  const longlong2* n2 = reinterpret_cast<const longlong2*>(r + 32);
+  const uint4* m4 = reinterpret_cast<const uint4*>(r + 32);
+  const int lim = NBT > 0 ? NBT : CRASH_MAX_BINS;
 #pragma unroll
-  for (int j = 0; j < (NBT > 0 ? (NBT + 1) / 2 : CRASH_MAX_BINS / 2); ++j) {
-    if (NBT == 0 && 2 * j >= nb) break;
-    const longlong2 v = n2[j];
-    N[2 * j] = v.x;
-    if (2 * j + 1 < (NBT > 0 ? NBT : CRASH_MAX_BINS)) N[2 * j + 1] = v.y;
+  for (int j = 0; j < (NBT > 0 ? (NBT + 3) / 4 : CRASH_MAX_BINS / 4); ++j) {
+    if (NBT == 0 && 4 * j >= nb) break;
+    const uint4 v = m4[j];
+    const int k = 4 * j;
+    c.m[k] = v.x;
+    if (k + 1 < lim) c.m[k + 1] = v.y;
+    if (k + 2 < lim) c.m[k + 2] = v.z;
+    if (k + 3 < lim) c.m[k + 3] = v.w;
   }
 }
 
@@ -416,7 +447,8 @@ __device__ __forceinline__ void load_record(const char* rec, int rs, long long i
 template <int NBT>
 __device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& w, bool alive, int ix,
                                                int iy, int iz, int box, float tMx, float tMy, float tMz,
-                                               float dx, float dy, float dz, const long long* N, int nb) {
+                                               float dx, float dy, float dz, const Content<NBT>& N,
+                                               int nb) {
   const long long slot = append_slot(alive, w.count_out);
   bool ok = alive;
   if (alive && slot >= w.cap) {
@@ -455,7 +487,8 @@ __global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables 
     bool alive = false;
     int ix = 0, iy = 0, iz = 0;
     float tMx = 0.f, tMy = 0.f, tMz = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    long long N[NBT > 0 ? NBT : CRASH_MAX_BINS];
+    Content<NBT> N;
+    N.e = 0;
     if (i < n) {
       const int64_t gid = g0 + i;
       b = box_of_packet(a.boxes, a.n_boxes, gid);
@@ -468,12 +501,21 @@ __global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables 
       if (!iso_direction_f32(M->seed, step, (uint32_t)s_local, p, fx, fy, fz)) {
         atomicOr(a.err, ERR_DIRECTION);
       } else {
+        // the packet's share of every bin in quanta, held as 32-bit counts
+        // in units of 2^e (the low e bits, below 2^-31 of the packet, are not
+        // emitted)
+        unsigned long long q[NBT > 0 ? NBT : CRASH_MAX_BINS];
+        unsigned long long qmax = 0;
         for (int j = 0; j < nb; ++j) {
           const long long base_c = a.src_base[(int64_t)s * nb + j];
           const long long rem = a.src_rem[(int64_t)s * nb + j];
-          N[j] = base_c + ((long long)p < rem ? 1 : 0);
-          tl.emitted += (unsigned long long)N[j];
+          q[j] = (unsigned long long)(base_c + ((long long)p < rem ? 1 : 0));
+          qmax = q[j] > qmax ? q[j] : qmax;
         }
+        const int bits = qmax ? 64 - __clzll((long long)qmax) : 0;
+        N.e = bits > 32 ? bits - 32 : 0;
+        for (int j = 0; j < nb; ++j) N.m[j] = (unsigned)(q[j] >> N.e);
+        tl.emitted += N.total(nb);
         tl.packets += 1;
         const float px = a.src_pos32[3 * s], py = a.src_pos32[3 * s + 1], pz = a.src_pos32[3 * s + 2];
         ix = a.src_cell[3 * s]; iy = a.src_cell[3 * s + 1]; iz = a.src_cell[3 * s + 2];
@@ -483,9 +525,7 @@ __global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables 
         tMz = fz > 0.f ? ((float)(iz + 1) - pz) / fz : (fz < 0.f ? ((float)iz - pz) / fz : INFINITY);
         const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
                                                  nb, S, tl);
-        if (r == ESCAPED) {
-          for (int j = 0; j < nb; ++j) tl.escaped += (unsigned long long)N[j];
-        }
+        if (r == ESCAPED) tl.escaped += N.total(nb);
         alive = (r == ALIVE);
       }
     }
@@ -508,16 +548,15 @@ __global__ void __launch_bounds__(256, MINB) k_pass_mixed(StepArgs a, BinTables 
     bool alive = false;
     int ix = 0, iy = 0, iz = 0;
     float tMx = 0.f, tMy = 0.f, tMz = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    long long N[NBT > 0 ? NBT : CRASH_MAX_BINS];
+    Content<NBT> N;
+    N.e = 0;
     if (j < n) {
       const int64_t i = w.perm ? (int64_t)w.perm[j] : j;
       load_record<NBT>(w.rec_in, w.rs, i, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
       const BoxMeta* M = a.boxes + b;
       const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
                                                nb, S, tl);
-      if (r == ESCAPED) {
-        for (int jj = 0; jj < nb; ++jj) tl.escaped += (unsigned long long)N[jj];
-      }
+      if (r == ESCAPED) tl.escaped += N.total(nb);
       alive = (r == ALIVE);
     }
     write_survivor<NBT>(a, w, alive, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
@@ -688,15 +727,14 @@ __global__ void __launch_bounds__(kTileBlock, 3) k_tile_pass(StepArgs a, BinTabl
       bool alive = false;
       int ix = 0, iy = 0, iz = 0;
       float tMx = 0.f, tMy = 0.f, tMz = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-      long long N[NBT > 0 ? NBT : CRASH_MAX_BINS];
+      Content<NBT> N;
+      N.e = 0;
       if (j < hi) {
         load_record<NBT>(w.rec_in, w.rs, (long long)w.perm[j], ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz,
                          N, nb);
         const int r = walk<NBT, HE, HEAT, true>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells, t, nb,
                                                 64, tl, x0, y0, z0, ex, ey, ez);
-        if (r == ESCAPED) {
-          for (int jj = 0; jj < nb; ++jj) tl.escaped += (unsigned long long)N[jj];
-        }
+        if (r == ESCAPED) tl.escaped += N.total(nb);
         alive = (r == ALIVE);
       }
       write_survivor<NBT>(a, w, alive, ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz, N, nb);
@@ -901,7 +939,7 @@ int launch_trace_mixed_external(const StepArgs& a, const BinTables& t, const cra
   WF wf;                       // views the caller's buffers; owns nothing
   wf.cap = cap;
   wf.nb = t.n_bins;
-  wf.rs = ((32 + 8 * t.n_bins) + 15) / 16 * 16;
+  wf.rs = ((32 + 4 * t.n_bins) + 15) / 16 * 16;
   wf.rec[0] = rec0;
   wf.rec[1] = rec1;
   wf.count = count;
@@ -916,7 +954,7 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
   WF* w = new WF();
   w->cap = cap;
   w->nb = nb;
-  w->rs = ((32 + 8 * nb) + 15) / 16 * 16;
+  w->rs = ((32 + 4 * nb) + 15) / 16 * 16;
   w->n_keys = n_keys;
   cudaError_t e = cudaMalloc(&w->count, 4 * sizeof(unsigned));
   if (e == cudaSuccess && cap > 0) {

@@ -92,7 +92,9 @@ def test_mixed_against_oracle_fields(thin):
     for _ in range(3):
         o.step(dt, P)
     bg, bo = g.read(native.F_BUDGET), o.read(oracle.F_BUDGET)
-    assert bg[0] == bo[0] and bg[0] == bg[1] + bg[2]
+    # the mixed form holds packet contents as 32-bit counts of 2^e quanta:
+    # it emits the same photons to 2^-31 per packet
+    assert bg[0] == bg[1] + bg[2] and abs(bg[0] - bo[0]) <= 1e-8 * bo[0]
     assert abs(bg[1] - bo[1]) <= 1e-5 * bo[0]
     assert abs(bg[3] - bo[3]) <= 1e-3 * bo[3]
     for fg, fo in STATE_FIELDS:
@@ -144,7 +146,7 @@ def test_mixed_full_size_512_window_against_oracle():
     o.set_options(chemistry=0, pkt_begin=0, pkt_end=2)
     o.step(w.dt_s, P)
     bg, bo = g.read(native.F_BUDGET), o.read(oracle.F_BUDGET)
-    assert bg[0] == bo[0] and bg[4] == bo[4] == 2 * box.n_src
+    assert abs(bg[0] - bo[0]) <= 1e-8 * bo[0] and bg[4] == bo[4] == 2 * box.n_src
     assert bg[0] == bg[1] + bg[2]
     assert abs(bg[1] - bo[1]) <= 1e-5 * bo[0]
     assert abs(bg[3] - bo[3]) <= 1e-3 * bo[3]
