@@ -357,9 +357,9 @@ def run_crash(args):
     value = cross_all / (ms_max * 1e-3)
 
     # roofline of the dominant (transport) kernel
-    bx = bytes_per_crossing(box, prec)
+    bpc = bytes_per_crossing(box, prec)
     peak, peak_kind = measured_peaks()
-    achieved = (crossings * bx) / (kms * 1e-3) / 1e9 if kms > 0 else None
+    achieved = (crossings * bpc) / (kms * 1e-3) / 1e9 if kms > 0 else None
     ksrc = os.path.join(ROOT, "paper_1101_4127_gb300", "csrc",
                         "k_fp64.cu" if prec == native.CRASH_FP64_PLAIN else "k_mixed.cu")
     dram_per_launch, cross_per_launch = traffic_for(args.workload, ksrc)
@@ -460,7 +460,7 @@ def run_crash(args):
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "whole step (graph replay)" if graph else "transport",
-                         "bytes_per_crossing": bx,
+                         "bytes_per_crossing": bpc,
                          "kernel_ms_per_launch": kms / max(1, klaunches)},
             "cpu_baseline": cpu,
             "e2e": e2e,

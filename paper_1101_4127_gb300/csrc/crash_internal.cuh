@@ -14,7 +14,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/crash.h"
+#include "crash.h"
 
 #define CRASH_MAX_BINS 16
 #define CRASH_MAX_BOXES 4096

@@ -11,10 +11,10 @@
 //
 // Two launch shapes:
 //   * one thread per packet (opts.wavefront = 0): emit and trace to the end;
-//   * wavefront (default): the emission kernel traces every packet for at
-//     most S DDA steps and appends the survivors to a device queue; pass
-//     kernels (persistent, grid-stride over the live count held in device
-//     memory) advance the queue S steps at a time until it is empty.  Every
+//   * wavefront (default): the emission kernel writes every packet to a
+//     device queue; pass kernels (persistent, grid-stride over the live
+//     count held in device memory) advance the queue S steps at a time until
+//     it is empty.  Every
 //     R passes the queue is re-sorted by Morton order of its 8^3-cell bucket
 //     and direction octant (one-pass counting sort), so that the packets a
 //     warp holds gather neighbouring cells.  Deposits are integer sums, so
@@ -204,24 +204,25 @@ __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 
     }
     left |= mj;
   }
-  // species split and heating rounded once per cell in the packet's units,
-  // then scaled to photon quanta
+  // species split and heating rounded once per cell in photon quanta (the
+  // FP32 sums are in the packet's units; scaling by 2^e is exact)
   long long a1 = 0, a2 = 0, h = 0;
-  const long long Au = (long long)At;
+  const long long Au = (long long)(At << c.e);
   if (At) {
+    const float unit = __uint_as_float((unsigned)(127 + c.e) << 23);
     if (HE) {
-      a1 = float_to_ll(fHeI);
+      a1 = float_to_ll(fHeI * unit);
       a1 = a1 > Au ? Au : a1;
-      a2 = float_to_ll(fHeII);
+      a2 = float_to_ll(fHeII * unit);
       a2 = a2 > Au - a1 ? Au - a1 : a2;
     }
-    if (HEAT) h = float_to_ll(fheat);
+    if (HEAT) h = float_to_ll(fheat * unit);
   }
-  dHeI = a1 << c.e;
-  dHeII = a2 << c.e;
-  dHI = (Au - a1 - a2) << c.e;
-  dE = h << c.e;
-  return Au << c.e;
+  dHeI = a1;
+  dHeII = a2;
+  dHI = Au - a1 - a2;
+  dE = h;
+  return Au;
 }
 
 // Where a walk reads absorbers and adds deposits: the grid in global memory
@@ -864,7 +865,9 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
   }
   const int S = o.seg_per_iter > 0 ? o.seg_per_iter : 32;
   const int R = o.resort_interval == 0 ? 1 : o.resort_interval;
-  const int passes = (max_iter + S - 1) / S;
+  // emission only writes the packets (no walk): every crossing is made by the
+  // passes, which read the queue in sorted order
+  const int passes = (max_iter + S - 1) / S + 1;
   const int nscan = (int)((wf->n_keys + 4095) / 4096);
   // the pass p (p >= 1) reads in sorted order when R > 0 and p % R == 0
   auto sorted_pass = [&](int p) { return p >= 1 && p < passes && R > 0 && (p % R) == 0; };
@@ -882,9 +885,9 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
         int64_t blocks = (n + block - 1) / block;
         if (blocks > persistent * 4) blocks = persistent * 4;
         if (o.reg_cap)
-          k_emit_mixed<NBT, HE, HEAT, 4><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, S, max_iter);
+          k_emit_mixed<NBT, HE, HEAT, 4><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
         else
-          k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, S, max_iter);
+          k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
       } else {
         if (o.reg_cap) k_pass_mixed<NBT, HE, HEAT, 4><<<persistent, block, 0, s>>>(a, t, w, S);
         else k_pass_mixed<NBT, HE, HEAT, 1><<<persistent, block, 0, s>>>(a, t, w, S);
