@@ -313,6 +313,8 @@ def run_crash(args):
     for k in range(args.warmup):
         one_step()
         if k == 0 and prec == native.CRASH_MIXED and not args.no_autotune:
+            if hold:
+                g.checkpoint(native.CKPT_RESTORE_STATE)   # tune on the state that is timed
             g.sync()
             tuned = g.autotune(w.dt_s, Plist)   # block, crossings per pass, re-sort, reg cap
             tuned_kw.update(block_size=tuned[0], seg_per_iter=tuned[1], resort_interval=tuned[2],

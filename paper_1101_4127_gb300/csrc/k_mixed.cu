@@ -473,8 +473,8 @@ __device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& 
 }
 
 // ------------------------------------------------------------------ emission
-// MINB = 4 caps the kernels at 64 registers (more resident warps to hide the
-// gather latency); MINB = 1 leaves the register count to the compiler.
+// MINB = 3 keeps three 256-thread blocks resident per SM (at most 85
+// registers); MINB = 4 caps the kernels at 64 registers for four.
 template <int NBT, bool HE, bool HEAT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables t, WFArgs w, int64_t g0,
                                                    int64_t n, int S, int max_steps_all) {
@@ -810,7 +810,7 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
       k_emit_mixed<NBT, HE, HEAT, 4><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
                                                                        max_iter, max_iter);
     else
-      k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
+      k_emit_mixed<NBT, HE, HEAT, 3><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
                                                                        max_iter, max_iter);
     toc();
     return 1;
@@ -835,7 +835,7 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
         int64_t blocks = (n + block - 1) / block;
         if (blocks > persistent * 4) blocks = persistent * 4;
         tic();
-        k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
+        k_emit_mixed<NBT, HE, HEAT, 3><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
         toc();
         ++launches;
         cur = 0;
@@ -887,10 +887,10 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
         if (o.reg_cap)
           k_emit_mixed<NBT, HE, HEAT, 4><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
         else
-          k_emit_mixed<NBT, HE, HEAT, 1><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
+          k_emit_mixed<NBT, HE, HEAT, 3><<<(unsigned)blocks, block, 0, s>>>(a, t, w, g0, n, 0, max_iter);
       } else {
         if (o.reg_cap) k_pass_mixed<NBT, HE, HEAT, 4><<<persistent, block, 0, s>>>(a, t, w, S);
-        else k_pass_mixed<NBT, HE, HEAT, 1><<<persistent, block, 0, s>>>(a, t, w, S);
+        else k_pass_mixed<NBT, HE, HEAT, 3><<<persistent, block, 0, s>>>(a, t, w, S);
       }
       toc();
       ++launches;
