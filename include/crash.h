@@ -102,11 +102,19 @@ typedef struct {
   int reg_cap;               /* mixed form: 1 = transport kernels capped at 64 registers
                                 (more resident warps), 0 = uncapped (tuned/default) */
   int tile;                  /* mixed form: 1 = tile passes (packets sorted into 16^3-cell
-                                tiles, absorbers and deposits of a tile staged in shared
-                                memory); 0 = passes of seg_per_iter cells over global memory */
+                                tiles, absorbers of a tile staged in shared memory); 0 = passes
+                                of seg_per_iter cells over global memory */
+  int pass_limit;            /* mixed form: at most this many wavefront passes per chunk
+                                (0 = as many as the grid needs).  A packet still alive after
+                                the last pass is a device-side limit: the next synchronising
+                                call returns CRASH_ERR_TIMEOUT. */
 } crash_run_opts;
 
 void crash_default_opts(crash_run_opts* o);
+
+/* Device memory of a context may be capped with the environment variable
+   CRASH_DEVICE_MEMORY_CAP (bytes): creation, sources or a step whose
+   allocations would exceed it fail with CRASH_ERR_OOM and allocate nothing. */
 
 /* Create a context holding one grid (equivalent to a batch of one). */
 crash_status crash_init_grid(const crash_grid_desc* desc, crash_ctx** out);

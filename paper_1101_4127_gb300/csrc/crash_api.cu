@@ -81,7 +81,15 @@ struct crash_ctx {
   int64_t n_tile_keys = 0;       // tile-pass keys over all boxes
   int max_tiles = 0;             // bound on the tiles one packet crosses
   int wf_mode = -1;              // wavefront option the workspace was sized for
+  size_t bytes = 0;              // device bytes allocated by the context
 };
+
+// optional cap on the device memory a context may allocate (bytes; 0 = none)
+static size_t memory_cap() {
+  const char* v = getenv("CRASH_DEVICE_MEMORY_CAP");
+  if (!v || !*v) return 0;
+  return (size_t)strtoull(v, nullptr, 10);
+}
 
 static crash_status set_err(crash_ctx* c, crash_status st, const std::string& msg) {
   if (c) c->error = msg;
@@ -295,6 +303,17 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
       {(void**)&c->err, sizeof(int)}, {(void**)&c->boxE, sizeof(int) * n_boxes}};
   if (c->precision == CRASH_MIXED) allocs.push_back({(void**)&c->abs32, n * 16});
   else allocs.push_back({(void**)&c->abs64, n * 32});
+  {
+    size_t want = 0;
+    for (auto& a : allocs) want += a.bytes;
+    const size_t cap = memory_cap();
+    if (cap && want > cap) {
+      g_create_error = "device memory cap (CRASH_DEVICE_MEMORY_CAP) exceeded: need " +
+                       std::to_string(want) + " bytes";
+      return fail(CRASH_ERR_OOM);
+    }
+    c->bytes = want;
+  }
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
@@ -628,6 +647,10 @@ extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t
       if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     }
     if (!c->wf) {
+      const size_t cap = memory_cap();
+      const size_t need = (size_t)want * (size_t)(2 * (((32 + 4 * c->n_bins) + 15) / 16 * 16) + 12);
+      if (cap && c->bytes + need > cap)
+        return set_err(c, CRASH_ERR_OOM, "device memory cap (CRASH_DEVICE_MEMORY_CAP) exceeded by the packet queue");
       cudaError_t e = cudaSuccess;
       c->wf = wavefront_create(want, c->n_keys, c->n_bins, &e);
       if (!c->wf) return set_err(c, CRASH_ERR_OOM, std::string("wavefront workspace: ") + cudaGetErrorString(e));

@@ -840,7 +840,8 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
         ++launches;
         cur = 0;
       }
-      for (int p = 1; p <= a.max_tiles; ++p) {
+      const int tile_passes = (o.pass_limit > 0 && o.pass_limit < a.max_tiles) ? o.pass_limit : a.max_tiles;
+      for (int p = 1; p <= tile_passes; ++p) {
         k_scan_blocks<<<nscan_t, 1024, 0, s>>>(wf->bcount, wf->boff, wf->bsum, nk);
         k_scan_sums<<<1, 1024, 0, s>>>(wf->bsum, nscan_t);
         k_scan_add<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(wf->boff, wf->bsum, nk);
@@ -867,7 +868,8 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
   const int R = o.resort_interval == 0 ? 1 : o.resort_interval;
   // emission only writes the packets (no walk): every crossing is made by the
   // passes, which read the queue in sorted order
-  const int passes = (max_iter + S - 1) / S + 1;
+  int passes = (max_iter + S - 1) / S + 1;
+  if (o.pass_limit > 0 && o.pass_limit < passes) passes = o.pass_limit;
   const int nscan = (int)((wf->n_keys + 4095) / 4096);
   // the pass p (p >= 1) reads in sorted order when R > 0 and p % R == 0
   auto sorted_pass = [&](int p) { return p >= 1 && p < passes && R > 0 && (p % R) == 0; };

@@ -171,3 +171,34 @@ def test_batch_64_recipe_graph_equals_separate_boxes():
             assert np.array_equal(x, y), i
     tot = sum(int(g.read(native.F_BUDGET, i)[0]) for i in range(len(w.boxes)))
     assert tot > 0
+
+
+def test_pass_limit_reports_timeout_status_and_fresh_context_works():
+    """A wavefront cut short (pass_limit) leaves packets alive: the bounded
+    device loop reports it as CRASH_ERR_TIMEOUT at the next synchronising
+    call instead of hanging; a new context is unaffected."""
+    box = small_hhe_box((24, 24, 24), n_src=2, seed=150, thin=True)
+    P = 2 * 5000
+    g = native.Grid(box, MIXED)
+    g.set_options(chemistry=0, seg_per_iter=4, pass_limit=2)
+    g.step(0.01 * inputs.MYR_S, P)
+    with pytest.raises(native.CrashError) as ei:
+        g.sync()
+    assert ei.value.status == native.CRASH_ERR_TIMEOUT
+    g.close()
+    h = native.Grid(box, MIXED)
+    h.step(0.01 * inputs.MYR_S, P)
+    b = h.read(native.F_BUDGET)
+    assert b[0] == b[1] + b[2]
+
+
+def test_memory_cap_gives_oom_status(monkeypatch):
+    box = small_hhe_box((16, 16, 16), n_src=1, seed=151)
+    monkeypatch.setenv("CRASH_DEVICE_MEMORY_CAP", "4096")
+    with pytest.raises(native.CrashError) as ei:
+        native.Grid(box, MIXED)
+    assert ei.value.status == native.CRASH_ERR_OOM
+    monkeypatch.setenv("CRASH_DEVICE_MEMORY_CAP", str(1 << 40))
+    g = native.Grid(box, MIXED)
+    g.step(0.01 * inputs.MYR_S, 1000)
+    assert g.read(native.F_BUDGET)[4] == 1000
