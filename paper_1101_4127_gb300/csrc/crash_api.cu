@@ -637,9 +637,12 @@ extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t
   CK(cudaMemcpyAsync(c->d_meta, c->meta.data(), sizeof(BoxMeta) * c->n_boxes,
                      cudaMemcpyHostToDevice, c->stream));
   if (c->precision == CRASH_MIXED) {
-    // packet queue: sized to the step (at most 2^26 packets per chunk); none
-    // when every packet is traced to the end by its own thread
-    const int64_t want = c->opts.wavefront ? std::min<int64_t>(total, (int64_t)1 << 26) : 0;
+    // packet queue: sized to the step (at most 2^28 packets per chunk, 38 GB
+    // with 8 bins); none when every packet is traced to the end by its own
+    // thread.  Larger chunks put more packets in each sort bucket of a pass,
+    // so more crossings of a cell fall close together in time and its
+    // deposit record is reused in L2.
+    const int64_t want = c->opts.wavefront ? std::min<int64_t>(total, (int64_t)1 << 28) : 0;
     if (c->wf && (c->wf_mode != c->opts.wavefront || wavefront_capacity(c->wf) < want)) {
       CK(cudaStreamSynchronize(c->stream));
       wavefront_destroy(c->wf);
@@ -823,7 +826,7 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   crash_run_opts base = c->opts;
   crash_run_opts best = base;
   double best_ms = 1e300;
-  // trials trace a window of about one wavefront chunk (2^26 packets) or less
+  // trials trace a window of about 2^26 packets (a quarter of a wavefront chunk) or less
   uint32_t win = 0xFFFFFFFFu;
   {
     int64_t tot = 0;

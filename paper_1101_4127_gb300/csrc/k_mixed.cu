@@ -158,7 +158,148 @@ struct Content {
   }
 };
 
+// Two FP32 lanes in one 64-bit register for the packed f32x2 arithmetic of
+// this GPU (fma/mul/add on both lanes in one instruction).  Each lane is
+// rounded exactly as the scalar instruction, so a pair of bins done packed
+// gives the same bits as the two bins done one by one.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_split(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 enum { ALIVE = 0, ABSORBED = 1, ESCAPED = 2 };
+
+// One bin's absorbed count once its optical depth tau and the series value
+// q = Nf (1 - e^-tau)/tau (tau < 0.5) are known: the same rounding as
+// absorb(), with the transmitted part taken for tau >= 0.5 (q replaced).
+__device__ __forceinline__ unsigned absorb_lane(unsigned m, float Nf, float tau, float& q) {
+  if (tau < 0.5f) {
+    const unsigned A = __float2uint_rn(q * tau);
+    return A > m ? m : A;
+  }
+  const float T = Nf * expf(-tau);
+  q = (Nf - T) * __fdividef(1.0f, tau);
+  unsigned Np = __float2uint_rn(T);
+  Np = Np > m ? m : Np;
+  return m - Np;
+}
+
+// cell_attenuate for an even number of bins, two bins per packed
+// instruction: the optical depths, the series and the heating weights of a
+// bin pair in f32x2, the rounding to counts and the running species and
+// heating sums per bin in bin order.  Gives the same bits as the scalar form.
+template <int NBT, bool HE, bool HEAT>
+__device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, float4 ab, Content<NBT>& c,
+                                                       const BinTables& t, long long& dHI,
+                                                       long long& dHeI, long long& dHeII, long long& dE,
+                                                       unsigned& left) {
+  static_assert(NBT >= 2 && NBT % 2 == 0, "bin pairs");
+  const float l = seg * dl;
+  const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
+  const f32x2 tHI2 = f2(tHI, tHI), tHeI2 = f2(tHeI, tHeI), tHeII2 = f2(tHeII, tHeII);
+  unsigned long long At = 0;
+  left = 0;
+  float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
+#pragma unroll
+  for (int j = 0; j < NBT; j += 2) {
+    const f32x2 s0 = f2(t.sigma32[0][j], t.sigma32[0][j + 1]);
+    const f32x2 k0 = f2_mul(tHI2, s0);
+    f32x2 tau = k0, k1 = 0ull, k2 = 0ull;
+    if (HE) {
+      const f32x2 s1 = f2(t.sigma32[1][j], t.sigma32[1][j + 1]);
+      const f32x2 s2 = f2(t.sigma32[2][j], t.sigma32[2][j + 1]);
+      k1 = f2_mul(tHeI2, s1);
+      k2 = f2_mul(tHeII2, s2);
+      tau = f2_fma(tHeII2, s2, f2_fma(tHeI2, s1, k0));
+    }
+    const unsigned m0 = c.m[j], m1 = c.m[j + 1];
+    const float N0 = __uint2float_rn(m0), N1 = __uint2float_rn(m1);
+    const f32x2 Nf = f2(N0, N1);
+    // (1 - e^-tau)/tau by the same Horner steps as absorbed_over_tau
+    f32x2 p = f2(-1.0f / 40320.0f, -1.0f / 40320.0f);
+    p = f2_fma(p, tau, f2(1.0f / 5040.0f, 1.0f / 5040.0f));
+    p = f2_fma(p, tau, f2(-1.0f / 720.0f, -1.0f / 720.0f));
+    p = f2_fma(p, tau, f2(1.0f / 120.0f, 1.0f / 120.0f));
+    p = f2_fma(p, tau, f2(-1.0f / 24.0f, -1.0f / 24.0f));
+    p = f2_fma(p, tau, f2(1.0f / 6.0f, 1.0f / 6.0f));
+    p = f2_fma(p, tau, f2(-0.5f, -0.5f));
+    p = f2_fma(p, tau, f2(1.0f, 1.0f));
+    float q0, q1, tau0, tau1;
+    f2_split(f2_mul(Nf, p), q0, q1);
+    f2_split(tau, tau0, tau1);
+    // a bin with no photons or no optical depth absorbs nothing and adds
+    // nothing below (q k = 0), as when the scalar form skips it
+    const unsigned A0 = absorb_lane(m0, N0, tau0, q0);
+    const unsigned A1 = absorb_lane(m1, N1, tau1, q1);
+    c.m[j] = m0 - A0;
+    c.m[j + 1] = m1 - A1;
+    At += A0;
+    At += A1;
+    left |= (m0 - A0) | (m1 - A1);
+    float a0, a1, b0, b1;
+    if (HE) {
+      f2_split(k1, a0, a1);
+      f2_split(k2, b0, b1);
+      fHeI = fmaf(q0, a0, fHeI);
+      fHeII = fmaf(q0, b0, fHeII);
+    }
+    if (HEAT) {
+      float w0, w1;
+      if (HE) {
+        const f32x2 w = f2_fma(k0, f2(t.wheat32[0][j], t.wheat32[0][j + 1]),
+                               f2_fma(k1, f2(t.wheat32[1][j], t.wheat32[1][j + 1]),
+                                      f2_mul(k2, f2(t.wheat32[2][j], t.wheat32[2][j + 1]))));
+        f2_split(w, w0, w1);
+        fheat = fmaf(q0, w0, fheat);
+      } else {
+        float c0, c1;
+        f2_split(k0, c0, c1);
+        fheat = fmaf(q0 * c0, t.wheat32[0][j], fheat);
+        fheat = fmaf(q1 * c1, t.wheat32[0][j + 1], fheat);
+      }
+      if (HE) {
+        fHeI = fmaf(q1, a1, fHeI);
+        fHeII = fmaf(q1, b1, fHeII);
+        fheat = fmaf(q1, w1, fheat);
+      }
+    } else if (HE) {
+      fHeI = fmaf(q1, a1, fHeI);
+      fHeII = fmaf(q1, b1, fHeII);
+    }
+  }
+  long long a1 = 0, a2 = 0, h = 0;
+  const long long Au = (long long)(At << c.e);
+  if (At) {
+    const float unit = __uint_as_float((unsigned)(127 + c.e) << 23);
+    if (HE) {
+      a1 = float_to_ll(fHeI * unit);
+      a1 = a1 > Au ? Au : a1;
+      a2 = float_to_ll(fHeII * unit);
+      a2 = a2 > Au - a1 ? Au - a1 : a2;
+    }
+    if (HEAT) h = float_to_ll(fheat * unit);
+  }
+  dHeI = a1;
+  dHeII = a2;
+  dHI = Au - a1 - a2;
+  dE = h;
+  return Au;
+}
 
 // Attenuation and deposition in one crossed cell (Sec. 2, Eq. 1) for a
 // segment of seg cells: updates the packet's bins and returns the absorbed
@@ -169,6 +310,8 @@ __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 
                                                     int nb, const BinTables& t, long long& dHI,
                                                     long long& dHeI, long long& dHeII, long long& dE,
                                                     unsigned& left) {
+  if constexpr (NBT >= 2 && NBT % 2 == 0)
+    return cell_attenuate_x2<NBT, HE, HEAT>(seg, dl, ab, c, t, dHI, dHeI, dHeII, dE, left);
   const float l = seg * dl;
   const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
   unsigned long long At = 0;
@@ -226,18 +369,54 @@ __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 
 }
 
 // Where a walk reads absorbers and adds deposits: the grid in global memory
-// (gathers and int64 reductions in L2) ...
+// (gathers through L1, deposits reduced in L2) ...
+//
+// The four int64 deposits of a crossing are one 32-byte record, so they go
+// to L2 as one bulk reduction (cp.reduce.async.bulk .add.u64) from a 32-byte
+// slot of shared memory per thread instead of four separate reductions.
+// Two slots alternate: a slot is rewritten only after the bulk operation
+// issued from it two crossings earlier has read it.  Integer sums do not
+// depend on their order, so the deposits are the same bits either way.
+// Without a slot (stage == nullptr: more than kStageThreads threads, or a
+// deposit array not aligned to 16 bytes) the thread uses plain reductions.
+constexpr int kStageThreads = 256;
+
+__device__ __forceinline__ void bulk_add_u64x4(unsigned long long* gdst, unsigned long long* slot,
+                                               long long a0, long long a1, long long a2, long long e) {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+  reinterpret_cast<ulonglong2*>(slot)[0] = make_ulonglong2((unsigned long long)a0, (unsigned long long)a1);
+  reinterpret_cast<ulonglong2*>(slot)[1] = make_ulonglong2((unsigned long long)a2, (unsigned long long)e);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(slot);
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], 32;"
+               :: "l"(gdst), "r"(sa) : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// wait for every bulk operation this thread issued (reads of shared memory
+// and the reductions in global memory)
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 struct GlobalCells {
   const float4* abs;
   unsigned long long* dep;
   int64_t coff;
   int nx, ny;
+  unsigned long long* stage;     // this thread's two 32-byte slots (shared), or nullptr
+  mutable int slot;
   __device__ __forceinline__ int64_t index(int ix, int iy, int iz) const {
     return coff + (ix + nx * (iy + ny * iz));
   }
   __device__ __forceinline__ float4 load(int64_t c, int, int, int) const { return __ldg(abs + c); }
   __device__ __forceinline__ void add(int64_t c, long long a0, long long a1, long long a2, long long e) const {
     unsigned long long* dp = dep + 4 * c;
+    if (stage) {
+      bulk_add_u64x4(dp, stage + 4 * slot, a0, a1, a2, e);
+      slot ^= 1;
+      return;
+    }
     if (a0) atomicAdd(dp + 0, (unsigned long long)a0);
     if (a1) atomicAdd(dp + 1, (unsigned long long)a1);
     if (a2) atomicAdd(dp + 2, (unsigned long long)a2);
@@ -245,25 +424,24 @@ struct GlobalCells {
   }
 };
 
-// ... or one 16^3-cell tile whose absorbers are staged in shared memory
-// (deposits still go to the grid: they stay in L2 while the tile is worked)
+// ... or one 16^3-cell tile whose absorbers and deposits are both held in
+// shared memory while the tile's packets cross it (cells indexed locally,
+// lx + 16 (ly + 16 lz)); the deposits are int64 atomics in shared memory,
+// one array of 4096 per species (so that lanes at different cells spread
+// over the banks), and go to the grid once per work item
 struct TileCells {
   const float4* sabs;              // shared, [16][16][16]
-  unsigned long long* dep;
-  int64_t coff;
-  int nx, ny, x0, y0, z0;
+  unsigned long long* sdep;        // shared, [4][16][16][16]
+  int x0, y0, z0;
   __device__ __forceinline__ int64_t index(int ix, int iy, int iz) const {
-    return coff + (ix + nx * (iy + ny * iz));
+    return (ix - x0) + 16 * ((iy - y0) + 16 * (iz - z0));
   }
-  __device__ __forceinline__ float4 load(int64_t, int ix, int iy, int iz) const {
-    return sabs[(ix - x0) + 16 * ((iy - y0) + 16 * (iz - z0))];
-  }
+  __device__ __forceinline__ float4 load(int64_t c, int, int, int) const { return sabs[c]; }
   __device__ __forceinline__ void add(int64_t c, long long a0, long long a1, long long a2, long long e) const {
-    unsigned long long* dp = dep + 4 * c;
-    if (a0) atomicAdd(dp + 0, (unsigned long long)a0);
-    if (a1) atomicAdd(dp + 1, (unsigned long long)a1);
-    if (a2) atomicAdd(dp + 2, (unsigned long long)a2);
-    if (e) atomicAdd(dp + 3, (unsigned long long)e);
+    if (a0) atomicAdd(sdep + c, (unsigned long long)a0);
+    if (a1) atomicAdd(sdep + 4096 + c, (unsigned long long)a1);
+    if (a2) atomicAdd(sdep + 8192 + c, (unsigned long long)a2);
+    if (e) atomicAdd(sdep + 12288 + c, (unsigned long long)e);
   }
 };
 
@@ -295,20 +473,18 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
   float4 ab = cells.load(cell, ix, iy, iz);
   for (int it = 1;; ++it) {
     // step the walk into the next cell and request its absorbers
-    tMx -= seg;
-    tMy -= seg;
-    tMz -= seg;
-    bool out, leave;
-    if (ax == 0) {
-      tMx = tDx; ix += sx; out = (unsigned)ix >= (unsigned)nx;
-      leave = TILE ? (unsigned)(ix - tx0) >= (unsigned)ex : out;
-    } else if (ax == 1) {
-      tMy = tDy; iy += sy; out = (unsigned)iy >= (unsigned)ny;
-      leave = TILE ? (unsigned)(iy - ty0) >= (unsigned)ey : out;
-    } else {
-      tMz = tDz; iz += sz; out = (unsigned)iz >= (unsigned)nz;
-      leave = TILE ? (unsigned)(iz - tz0) >= (unsigned)ez : out;
-    }
+    const bool bx = ax == 0, by = ax == 1, bz = ax == 2;
+    tMx = bx ? tDx : tMx - seg;
+    tMy = by ? tDy : tMy - seg;
+    tMz = bz ? tDz : tMz - seg;
+    ix += bx ? sx : 0;
+    iy += by ? sy : 0;
+    iz += bz ? sz : 0;
+    const bool out = ((unsigned)ix >= (unsigned)nx) | ((unsigned)iy >= (unsigned)ny) |
+                     ((unsigned)iz >= (unsigned)nz);
+    const bool leave = TILE ? (((unsigned)(ix - tx0) >= (unsigned)ex) | ((unsigned)(iy - ty0) >= (unsigned)ey) |
+                               ((unsigned)(iz - tz0) >= (unsigned)ez))
+                            : out;
     float seg_n = 0.f;
     int ax_n = 0;
     int64_t cell_n = cell;
@@ -349,9 +525,14 @@ __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx
                                            const float dz, Content<NBT>& N, const BoxMeta* M,
                                            const StepArgs& a, const BinTables& t, const int nb,
                                            const int max_iter, Tally& tl) {
-  GlobalCells cells{reinterpret_cast<const float4*>(a.abs32), a.dep, M->cell_off, M->nx, M->ny};
-  return walk<NBT, HE, HEAT, false>(ix, iy, iz, tMx, tMy, tMz, dx, dy, dz, N, M, cells, t, nb,
-                                    max_iter, tl);
+  __shared__ __align__(16) unsigned long long stage[kStageThreads * 8];
+  const bool bulk = threadIdx.x < kStageThreads && ((uintptr_t)a.dep & 15u) == 0;
+  GlobalCells cells{reinterpret_cast<const float4*>(a.abs32), a.dep, M->cell_off, M->nx, M->ny,
+                    bulk ? stage + 8 * threadIdx.x : nullptr, 0};
+  const int r = walk<NBT, HE, HEAT, false>(ix, iy, iz, tMx, tMy, tMz, dx, dy, dz, N, M, cells, t, nb,
+                                           max_iter, tl);
+  if (bulk) bulk_wait_all();
+  return r;
 }
 
 // warp-aggregated append of surviving packets to the output queue
@@ -639,9 +820,9 @@ __global__ void k_perm(const unsigned* count, const unsigned* key, const unsigne
 }
 
 // ------------------------------------------------------------------ tiles
-constexpr int kTileItem = 2048;        // packets of a tile handled by one block visit
-constexpr int kTileBlock = 256;
-constexpr size_t kTileSmem = 4096 * sizeof(float4);
+constexpr int kTileItem = 8192;        // packets of a tile handled by one block visit
+constexpr int kTileBlock = 768;        // one block per SM (shared memory)
+constexpr size_t kTileSmem = 4096 * sizeof(float4) + 4096 * 4 * sizeof(unsigned long long);
 
 __device__ __forceinline__ unsigned compact3(unsigned v) {   // every third bit -> 10 bits
   v &= 0x09249249u;
@@ -683,18 +864,27 @@ __global__ void k_tile_list(const unsigned* boff, const unsigned* count, int64_t
   }
 }
 
-// One tile pass: a block takes the next work item, copies the tile's 16^3
-// absorbers into shared memory and walks each of the item's packets until it
-// leaves the tile (or is absorbed or escapes); deposits go to the grid.
-// Survivors go to the output queue with the key of the tile they enter.
+// One tile pass: a block takes the next work item (up to kTileItem packets
+// of one 16^3 tile), stages the tile's absorbers in shared memory with its
+// deposits zeroed, and its warps take the item's packets 32 at a time and
+// walk each until it leaves the tile (or is absorbed or escapes).  Deposits
+// are int64 atomics in shared memory; once the item is done every cell that
+// received any adds it to the grid with one reduction per species, so the
+// grid's deposit array is touched once per item instead of once per
+// crossing.  Sums of integers do not depend on their order: the deposits
+// are the same bits as with per-crossing reductions.  Survivors go to the
+// output queue with the key of the tile they enter.
 template <int NBT, bool HE, bool HEAT>
-__global__ void __launch_bounds__(kTileBlock, 3) k_tile_pass(StepArgs a, BinTables t, WFArgs w,
+__global__ void __launch_bounds__(kTileBlock, 1) k_tile_pass(StepArgs a, BinTables t, WFArgs w,
                                                              const unsigned* boff, const uint2* items,
                                                              const unsigned* nitems, unsigned* next,
                                                              int64_t n_keys) {
   extern __shared__ __align__(16) unsigned char smem[];
   float4* sabs = reinterpret_cast<float4*>(smem);
-  __shared__ unsigned s_item;
+  unsigned long long* sdep = reinterpret_cast<unsigned long long*>(smem + 4096 * sizeof(float4));
+  __shared__ unsigned s_item, s_next;
+  const unsigned full = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const unsigned nit = *nitems;
   const float4* abs32 = reinterpret_cast<const float4*>(a.abs32);
@@ -719,11 +909,20 @@ __global__ void __launch_bounds__(kTileBlock, 3) k_tile_pass(StepArgs a, BinTabl
       if (lx < ex && ly < ey && lz < ez)
         v = __ldg(abs32 + M->cell_off + (x0 + lx) + M->nx * ((y0 + ly) + M->ny * (z0 + lz)));
       sabs[li] = v;
+      sdep[li] = 0ull;
+      sdep[4096 + li] = 0ull;
+      sdep[8192 + li] = 0ull;
+      sdep[12288 + li] = 0ull;
     }
+    if (threadIdx.x == 0) s_next = lo;
     __syncthreads();
-    const TileCells cells{sabs, a.dep, M->cell_off, M->nx, M->ny, x0, y0, z0};
-    for (unsigned base = lo; base < hi; base += blockDim.x) {
-      const unsigned j = base + threadIdx.x;
+    const TileCells cells{sabs, sdep, x0, y0, z0};
+    for (;;) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(&s_next, 32u);
+      base = __shfl_sync(full, base, 0);
+      if (base >= hi) break;
+      const unsigned j = base + lane;
       int pb = -1;
       bool alive = false;
       int ix = 0, iy = 0, iz = 0;
@@ -740,6 +939,19 @@ __global__ void __launch_bounds__(kTileBlock, 3) k_tile_pass(StepArgs a, BinTabl
       }
       write_survivor<NBT>(a, w, alive, ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz, N, nb);
       flush_warp(a, pb, tl);
+    }
+    __syncthreads();
+    // the item's deposits to the grid, cell by cell
+    for (int li = threadIdx.x; li < 4096; li += blockDim.x) {
+      const int lx = li & 15, ly = (li >> 4) & 15, lz = li >> 8;
+      if (lx < ex && ly < ey && lz < ez) {
+        unsigned long long* g = a.dep + 4 * (M->cell_off + (x0 + lx) + (int64_t)M->nx * ((y0 + ly) + (int64_t)M->ny * (z0 + lz)));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const unsigned long long v = sdep[4096 * k + li];
+          if (v) atomicAdd(g + k, v);
+        }
+      }
     }
     __syncthreads();
   }
@@ -853,7 +1065,7 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
         WFArgs w = wf_args(wf, cur, true, true, 1);
         cudaMemsetAsync(w.count_out, 0, sizeof(unsigned), s);
         tic();
-        k_tile_pass<NBT, HE, HEAT><<<num_sms() * 3, kTileBlock, kTileSmem, s>>>(
+        k_tile_pass<NBT, HE, HEAT><<<num_sms(), kTileBlock, kTileSmem, s>>>(
             a, t, w, wf->boff, wf->items, wf->count + 2, wf->count + 3, nk);
         toc();
         launches += 6;
