@@ -372,6 +372,10 @@ void cross_sections(int nb, const double* E, BinTables& t, int& heatF) {
       t.sigma32[s][j] = (float)t.sigma[s][j];
       t.wheat32[s][j] = (float)t.wheat[s][j];
     }
+  for (int s = 0; s < 3; ++s) {
+    t.sigma32_max[s] = 0.f;
+    for (int j = 0; j < nb; ++j) t.sigma32_max[s] = std::max(t.sigma32_max[s], t.sigma32[s][j]);
+  }
   t.n_bins = nb;
 }
 

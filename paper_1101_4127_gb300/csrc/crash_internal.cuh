@@ -59,6 +59,7 @@ struct BinTables {
   double wheat[3][CRASH_MAX_BINS];   // (E_j - E_th,s) / 2^F, or 0 below threshold
   float sigma32[3][CRASH_MAX_BINS];
   float wheat32[3][CRASH_MAX_BINS];
+  float sigma32_max[3];              // largest sigma32 of each species over the bins
 };
 
 struct StepArgs {

@@ -203,18 +203,15 @@ __device__ __forceinline__ unsigned absorb_lane(unsigned m, float Nf, float tau,
 // instruction: the optical depths, the series and the heating weights of a
 // bin pair in f32x2, the rounding to counts and the running species and
 // heating sums per bin in bin order.  Gives the same bits as the scalar form.
-template <int NBT, bool HE, bool HEAT>
-__device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, float4 ab, Content<NBT>& c,
-                                                       const BinTables& t, long long& dHI,
-                                                       long long& dHeI, long long& dHeII, long long& dE,
-                                                       unsigned& left) {
-  static_assert(NBT >= 2 && NBT % 2 == 0, "bin pairs");
-  const float l = seg * dl;
-  const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
-  const f32x2 tHI2 = f2(tHI, tHI), tHeI2 = f2(tHeI, tHeI), tHeII2 = f2(tHeII, tHeII);
-  unsigned long long At = 0;
-  left = 0;
-  float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
+//
+// THIN: every bin of the cell has tau < 0.5 (known from one bound for the
+// whole cell), so every bin takes the series and A = rint(m (1 - e^-tau))
+// needs no clamp: it is at most 0.4 m + 1/2, below m for m >= 1.
+template <int NBT, bool HE, bool HEAT, bool THIN>
+__device__ __forceinline__ void attenuate_bins_x2(const f32x2 tHI2, const f32x2 tHeI2, const f32x2 tHeII2,
+                                                  Content<NBT>& c, const BinTables& t,
+                                                  unsigned long long& At, unsigned& left, float& fHeI,
+                                                  float& fHeII, float& fheat) {
 #pragma unroll
   for (int j = 0; j < NBT; j += 2) {
     const f32x2 s0 = f2(t.sigma32[0][j], t.sigma32[0][j + 1]);
@@ -239,13 +236,23 @@ __device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, floa
     p = f2_fma(p, tau, f2(1.0f / 6.0f, 1.0f / 6.0f));
     p = f2_fma(p, tau, f2(-0.5f, -0.5f));
     p = f2_fma(p, tau, f2(1.0f, 1.0f));
-    float q0, q1, tau0, tau1;
-    f2_split(f2_mul(Nf, p), q0, q1);
-    f2_split(tau, tau0, tau1);
+    const f32x2 q2 = f2_mul(Nf, p);
+    float q0, q1;
+    f2_split(q2, q0, q1);
     // a bin with no photons or no optical depth absorbs nothing and adds
     // nothing below (q k = 0), as when the scalar form skips it
-    const unsigned A0 = absorb_lane(m0, N0, tau0, q0);
-    const unsigned A1 = absorb_lane(m1, N1, tau1, q1);
+    unsigned A0, A1;
+    if (THIN) {
+      float qt0, qt1;
+      f2_split(f2_mul(q2, tau), qt0, qt1);
+      A0 = __float2uint_rn(qt0);
+      A1 = __float2uint_rn(qt1);
+    } else {
+      float tau0, tau1;
+      f2_split(tau, tau0, tau1);
+      A0 = absorb_lane(m0, N0, tau0, q0);
+      A1 = absorb_lane(m1, N1, tau1, q1);
+    }
     c.m[j] = m0 - A0;
     c.m[j + 1] = m1 - A1;
     At += A0;
@@ -282,6 +289,28 @@ __device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, floa
       fHeII = fmaf(q1, b1, fHeII);
     }
   }
+}
+
+template <int NBT, bool HE, bool HEAT>
+__device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, float4 ab, Content<NBT>& c,
+                                                       const BinTables& t, long long& dHI,
+                                                       long long& dHeI, long long& dHeII, long long& dE,
+                                                       unsigned& left) {
+  static_assert(NBT >= 2 && NBT % 2 == 0, "bin pairs");
+  const float l = seg * dl;
+  const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
+  const f32x2 tHI2 = f2(tHI, tHI), tHeI2 = f2(tHeI, tHeI), tHeII2 = f2(tHeII, tHeII);
+  unsigned long long At = 0;
+  left = 0;
+  float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
+  // the optical depth of every bin is at most this bound, computed with the
+  // largest cross sections in the same operation order (rounding is monotone)
+  const float k0max = tHI * t.sigma32_max[0];
+  const float tau_max = HE ? fmaf(tHeII, t.sigma32_max[2], fmaf(tHeI, t.sigma32_max[1], k0max)) : k0max;
+  if (tau_max < 0.5f)
+    attenuate_bins_x2<NBT, HE, HEAT, true>(tHI2, tHeI2, tHeII2, c, t, At, left, fHeI, fHeII, fheat);
+  else
+    attenuate_bins_x2<NBT, HE, HEAT, false>(tHI2, tHeI2, tHeII2, c, t, At, left, fHeI, fHeII, fheat);
   long long a1 = 0, a2 = 0, h = 0;
   const long long Au = (long long)(At << c.e);
   if (At) {
