@@ -97,13 +97,14 @@ __device__ __forceinline__ void flush_warp(const StepArgs& a, int b, Tally& t) {
 
 // FP32 <-> integer conversions without the hardware 64-bit conversions,
 // which on this GPU issue to the narrow FP64 pipe.
-// rint(x) for x in [0, 2^63), round half to even
+// rint(x) for x in [0, 2^63), round half to even, from two 32-bit
+// conversions: hi = floor(x / 2^32) and the rest x - hi 2^32, which the fma
+// gives exactly (below 2^32 the rest is x itself; above it x is an integer
+// whose low part fits the 24-bit significand, or hi holds all of x).
 __device__ __forceinline__ long long float_to_ll(float x) {
-  if (x < 8388608.0f)   // below 2^23 adding 2^23 rounds to an integer in the last place
-    return (long long)(__float_as_uint(x + 8388608.0f) - 0x4B000000u);
-  const unsigned b = __float_as_uint(x);
-  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-  return (long long)(m << ((int)(b >> 23) - 150));
+  const unsigned hi = __float2uint_rz(x * 2.3283064365386963e-10f);
+  const unsigned lo = __float2uint_rn(fmaf(-__uint2float_rn(hi), 4294967296.0f, x));
+  return (long long)(((unsigned long long)hi << 32) | lo);
 }
 
 // (1 - exp(-tau)) / tau for 0 < tau < 0.5 by its Taylor series to tau^7
