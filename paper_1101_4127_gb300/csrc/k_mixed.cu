@@ -318,9 +318,13 @@ __device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, floa
     const float unit = __uint_as_float((unsigned)(127 + c.e) << 23);
     if (HE) {
       a1 = float_to_ll(fHeI * unit);
-      a1 = a1 > Au ? Au : a1;
       a2 = float_to_ll(fHeII * unit);
-      a2 = a2 > Au - a1 ? Au - a1 : a2;
+      // He shares above the cell's total only by rounding: clamp then (the
+      // clamps change nothing when the two fit)
+      if ((unsigned long long)a1 + (unsigned long long)a2 > (unsigned long long)Au) {
+        a1 = a1 > Au ? Au : a1;
+        a2 = a2 > Au - a1 ? Au - a1 : a2;
+      }
     }
     if (HEAT) h = float_to_ll(fheat * unit);
   }
