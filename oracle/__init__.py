@@ -25,6 +25,7 @@ _lib = None
 F_XHII, F_XHEII, F_XHEIII, F_T = 0, 1, 2, 3
 F_DEP_HI, F_DEP_HEI, F_DEP_HEII, F_DEP_E = 4, 5, 6, 7
 F_BUDGET, F_NH = 8, 9
+F_REC_HI, F_REC_HEI, F_REC_HEII = 11, 12, 13
 C_COLL_EXC, C_COLL_ION, C_RECOMB, C_BREMS, C_COMPTON, C_DIELEC, C_ALL = 1, 2, 4, 8, 16, 32, 63
 
 
@@ -49,7 +50,7 @@ class GridDesc(C.Structure):
                 ("x_HeIII", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double)),
                 ("x_HII0", C.c_double), ("x_HeII0", C.c_double), ("x_HeIII0", C.c_double),
                 ("T0", C.c_double), ("isothermal", C.c_int), ("caseB", C.c_int),
-                ("z_compton", C.c_double), ("seed", C.c_uint64)]
+                ("z_compton", C.c_double), ("seed", C.c_uint64), ("f_rec", C.c_double)]
 
 
 class ChemCell(C.Structure):
@@ -58,7 +59,8 @@ class ChemCell(C.Structure):
                 ("T", C.c_double), ("G_HI", C.c_double), ("G_HeI", C.c_double),
                 ("G_HeII", C.c_double), ("heat_per_ion", C.c_double),
                 ("isothermal", C.c_int), ("caseB", C.c_int), ("T_cmb", C.c_double),
-                ("eps", C.c_double), ("max_sub", C.c_int), ("cool_mask", C.c_int)]
+                ("eps", C.c_double), ("max_sub", C.c_int), ("cool_mask", C.c_int),
+                ("count_rec", C.c_int), ("rec", C.c_double * 3)]
 
 
 def lib():
@@ -95,6 +97,7 @@ def lib():
             L.or_rates.restype = None
             L.or_compton_coef.argtypes = [C.c_double]
             L.or_compton_coef.restype = C.c_double
+            L.or_rec_start.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_int, dp, dp]
             _lib = L
     return _lib
 
@@ -142,17 +145,28 @@ def compton_coef(T_cmb: float) -> float:
 
 def chem_cell(dt: float, **kw):
     """Integrate one cell; keyword fields of ChemCell (defaults: isothermal 0,
-    caseB 1, eps 0.1, max_sub 10000, all processes on).  Returns (state dict,
-    sub-steps)."""
+    caseB 1, eps 0.1, max_sub 10000, all processes on, no recombination
+    count).  Returns (state dict, sub-steps); with count_rec=1 the dict also
+    holds 'rec', the recombinations to the ground state per cm^3 into H I,
+    He I, He II."""
     c = ChemCell()
     defaults = dict(nH=1e-3, nHe=0.0, xHII=0.0, xHeII=0.0, xHeIII=0.0, T=1e4, G_HI=0.0,
                     G_HeI=0.0, G_HeII=0.0, heat_per_ion=0.0, isothermal=0, caseB=1,
-                    T_cmb=0.0, eps=0.1, max_sub=10000, cool_mask=C_ALL)
+                    T_cmb=0.0, eps=0.1, max_sub=10000, cool_mask=C_ALL, count_rec=0)
     defaults.update(kw)
     for k, v in defaults.items():
         setattr(c, k, v)
     n = lib().or_chem_cell(C.byref(c), float(dt))
-    return {k: getattr(c, k) for k in ("xHII", "xHeII", "xHeIII", "T")}, n
+    out = {k: getattr(c, k) for k in ("xHII", "xHeII", "xHeIII", "T")}
+    out["rec"] = np.array(list(c.rec))
+    return out, n
+
+
+def rec_start(seed: int, step: int, cell: int, nx: int, ny: int):
+    """Start point (grid units) and direction of a cell's re-emission packet."""
+    pos, d = np.zeros(3), np.zeros(3)
+    k = lib().or_rec_start(seed, step, cell, nx, ny, _dptr(pos), _dptr(d))
+    return pos, d, k
 
 
 # ------------------------------------------------------------ grid context
@@ -163,7 +177,7 @@ class OracleGrid:
     def __init__(self, nx, ny, nz, box_cm, n_H=None, n_H0=1e-3, he_over_h=0.0,
                  x_HII=None, x_HeII=None, x_HeIII=None, T=None,
                  x_HII0=0.0, x_HeII0=0.0, x_HeIII0=0.0, T0=1e4,
-                 isothermal=0, caseB=1, z_compton=-1.0, seed=0):
+                 isothermal=0, caseB=1, z_compton=-1.0, seed=0, f_rec=0.0):
         self.L = lib()
         self.shape = (nz, ny, nx)
         self.ncell = nx * ny * nz
@@ -188,6 +202,7 @@ class OracleGrid:
         d.T = fp(T, np.float64, C.c_double)
         d.x_HII0, d.x_HeII0, d.x_HeIII0, d.T0 = x_HII0, x_HeII0, x_HeIII0, T0
         d.isothermal, d.caseB, d.z_compton, d.seed = isothermal, caseB, z_compton, seed
+        d.f_rec = f_rec
         self.ctx = self.L.oracle_init_grid(C.byref(d))
         if not self.ctx:
             raise RuntimeError("oracle_init_grid failed")
@@ -198,7 +213,8 @@ class OracleGrid:
         g = cls(nx, ny, nz, box.box_cm, n_H=box.nH, n_H0=box.nH0,
                 he_over_h=box.he_over_h, x_HII0=box.x_HII0, x_HeII0=box.x_HeII0,
                 x_HeIII0=box.x_HeIII0, T0=box.T0, isothermal=box.isothermal,
-                caseB=box.caseB, z_compton=box.z_compton, seed=box.seed)
+                caseB=box.caseB, z_compton=box.z_compton, seed=box.seed,
+                f_rec=getattr(box, "f_rec", 0.0))
         g.add_sources(box.src_pos, box.src_ndot, box.bin_eV, box.bin_frac)
         return g
 

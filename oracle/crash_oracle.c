@@ -55,6 +55,8 @@ struct or_ctx {
   int isothermal, caseB;
   double T_cmb;
   uint64_t seed;
+  double f_rec;                               /* > 0: diffuse recombination field */
+  double *rec[3];                             /* ground-state recombination photons */
   double *nH, *xHII, *xHeII, *xHeIII, *T;
   double *aHI, *aHeI, *aHeII;                 /* frozen absorber densities */
   int64_t *dHI, *dHeI, *dHeII, *dE;           /* per-step deposits */
@@ -128,6 +130,33 @@ int or_direction(uint64_t seed, uint32_t step, uint32_t src, uint32_t pkt, doubl
   return -1;
 }
 
+/* Start of the re-emission packet of a cell (the diffuse recombination
+   field of Sec. 2): a point drawn uniformly in the cell and an isotropic
+   direction.  The Philox counters are those of a source with index
+   0x80000000 | (cell >> 32) and packet cell & 0xffffffff, so no point source
+   shares them: the direction takes attempts 0..63 as for a source packet,
+   the offsets in the cell take attempts 64 (x, y) and 65 (z), each the top
+   31 bits of a 64-bit word times 2^-31, so that cell + offset is exact and
+   stays inside the cell. */
+static double u31(uint32_t lo, uint32_t hi) {
+  uint64_t w = ((uint64_t)hi << 32) | lo;
+  return (double)(w >> 33) * 0x1.0p-31;
+}
+
+int or_rec_start(uint64_t seed, uint32_t step, int64_t cell, int nx, int ny, double pos[3],
+                 double dir[3]) {
+  const uint32_t src = 0x80000000u | (uint32_t)((uint64_t)cell >> 32), pkt = (uint32_t)cell;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t c0[4] = {pkt, src, step, 64u}, c1[4] = {pkt, src, step, 65u}, r0[4], r1[4];
+  or_philox4x32_10(c0, key, r0);
+  or_philox4x32_10(c1, key, r1);
+  const int64_t ix = cell % nx, iy = (cell / nx) % ny, iz = cell / ((int64_t)nx * ny);
+  pos[0] = (double)ix + u31(r0[0], r0[1]);
+  pos[1] = (double)iy + u31(r0[2], r0[3]);
+  pos[2] = (double)iz + u31(r1[0], r1[1]);
+  return or_direction(seed, step, src, pkt, dir);
+}
+
 /* ------------------------------------------------------------ exp(-tau) */
 /* exp(-tau) for tau >= 0 by Cody-Waite range reduction and a Taylor
    polynomial: k = rint(x / ln 2), r = (x - k ln2_hi) - k ln2_lo with
@@ -195,13 +224,16 @@ or_ctx* oracle_init_grid(const or_grid_desc* d) {
   c->isothermal = d->isothermal; c->caseB = d->caseB;
   c->T_cmb = d->z_compton >= 0 ? 2.725 * (1.0 + d->z_compton) : 0.0;
   c->seed = d->seed;
+  c->f_rec = d->f_rec > 0 ? d->f_rec : 0.0;
   size_t n = (size_t)c->ncell;
   c->nH = malloc(n * 8); c->xHII = malloc(n * 8); c->xHeII = malloc(n * 8);
   c->xHeIII = malloc(n * 8); c->T = malloc(n * 8);
   c->aHI = calloc(n, 8); c->aHeI = calloc(n, 8); c->aHeII = calloc(n, 8);
   c->dHI = calloc(n, 8); c->dHeI = calloc(n, 8); c->dHeII = calloc(n, 8); c->dE = calloc(n, 8);
+  for (int a = 0; a < 3; ++a) c->rec[a] = calloc(n, 8);
   if (!c->nH || !c->xHII || !c->xHeII || !c->xHeIII || !c->T || !c->aHI || !c->aHeI ||
-      !c->aHeII || !c->dHI || !c->dHeI || !c->dHeII || !c->dE) {
+      !c->aHeII || !c->dHI || !c->dHeI || !c->dHeII || !c->dE || !c->rec[0] || !c->rec[1] ||
+      !c->rec[2]) {
     oracle_free(c);
     return NULL;
   }
@@ -224,6 +256,7 @@ void oracle_free(or_ctx* c) {
   free(c->nH); free(c->xHII); free(c->xHeII); free(c->xHeIII); free(c->T);
   free(c->aHI); free(c->aHeI); free(c->aHeII);
   free(c->dHI); free(c->dHeI); free(c->dHeII); free(c->dE);
+  free(c->rec[0]); free(c->rec[1]); free(c->rec[2]);
   free(c->pos); free(c->ndot); free(c->binE); free(c->binFrac);
   free(c);
 }
@@ -478,7 +511,7 @@ int or_chem_cell(or_chem_t* c, double dt) {
   double x = c->xHII, y2 = c->xHeII, y3 = c->xHeIII, T = c->T;
   double rem = dt;
   int nsub = 0;
-  double r[17];
+  double r[17], rB[17];
   while (rem > 0) {
     or_rates(T, c->caseB, r);
     double aH = use_rec ? r[0] : 0.0, aHe2 = use_rec ? r[1] + ((mask & OR_C_DIELEC) ? r[3] : 0.0) : 0.0;
@@ -559,6 +592,21 @@ int or_chem_cell(or_chem_t* c, double dt) {
       double ntot2 = nH + nHe + nen2;
       T = (1.5 * K_B * ntot * T + h * (heat + C * c->T_cmb)) / (1.5 * K_B * ntot2 + h * (L1 + C));
     }
+    if (c->count_rec && use_rec) {
+      /* recombinations straight to the ground state, alpha_A - alpha_B of
+         each ion (at least 0), with n_e and the ions at the end of the
+         sub-step as in the backward-Euler update */
+      or_rates(T, 1, rB);
+      double gH = r[0] - rB[0], g2 = r[1] - rB[1], g3 = r[2] - rB[2];
+      if (gH < 0.0) gH = 0.0;
+      if (g2 < 0.0) g2 = 0.0;
+      if (g3 < 0.0) g3 = 0.0;
+      c->rec[0] += h * gH * nen2 * (nH * xn);
+      if (nHe > 0) {
+        c->rec[1] += h * g2 * nen2 * (nHe * y2n);
+        c->rec[2] += h * g3 * nen2 * (nHe * y3n);
+      }
+    }
     x = xn; y2 = y2n; y3 = y3n;
     rem = (h == rem) ? 0.0 : rem - h;
     ++nsub;
@@ -584,6 +632,9 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
   for (int s = 0; s < c->n_src; ++s) if (c->ndot[s] > mx) mx = c->ndot[s];
   double X = ((double)c->n_src * mx) * dt;
   int E = X > 0 ? ceil_log2(X) - 62 : 0;
+  /* with the diffuse field on, two more bits of room for the re-emitted
+     photons (a step re-emits at most what earlier steps absorbed) */
+  if (c->f_rec > 0) E += 2;
   c->budget[5] = E;
   c->budget[6] = c->heatF;
 
@@ -625,6 +676,49 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
       ++traced;
     }
   }
+  if (c->f_rec > 0) {
+    /* diffuse recombination radiation (Sec. 2): every cell where the
+       recombinations to the ground state of some species reach f_rec times
+       that element's atoms in the cell re-emits them as one packet, and the
+       species' count restarts from zero.  The photons of a species go to the
+       lowest bin at or above its ionisation threshold (its Milne spectrum
+       lies within a few kT of the threshold); in quanta q of this step. */
+    const double V = (c->dl * c->dl) * c->dl;
+    const double q = ldexp(1.0, E);
+    int rec_bin[3];
+    for (int a = 0; a < 3; ++a) {
+      rec_bin[a] = -1;
+      for (int j = 0; j < nb; ++j)
+        if (c->binE[j] >= E_TH[a] && (rec_bin[a] < 0 || c->binE[j] < c->binE[rec_bin[a]]))
+          rec_bin[a] = j;
+    }
+    for (int64_t i = 0; i < c->ncell; ++i) {
+      const double atoms[3] = {c->nH[i] * V, c->nH[i] * c->he_over_h * V,
+                               c->nH[i] * c->he_over_h * V};
+      int64_t Nq[3] = {0, 0, 0};
+      int any = 0;
+      for (int a = 0; a < 3; ++a)
+        if (atoms[a] > 0 && c->rec[a][i] > 0 && c->rec[a][i] >= c->f_rec * atoms[a]) {
+          Nq[a] = llrint(c->rec[a][i] / q);
+          c->rec[a][i] = 0.0;
+          any = 1;
+        }
+      if (!any) continue;
+      for (int j = 0; j < nb; ++j) N[j] = 0;
+      int64_t tot = 0;
+      for (int a = 0; a < 3; ++a)
+        if (rec_bin[a] >= 0 && Nq[a] > 0) { N[rec_bin[a]] += Nq[a]; tot += Nq[a]; }
+      if (tot == 0) continue;
+      double pos[3], d[3];
+      if (or_rec_start(c->seed, (uint32_t)c->step, i, c->nx, c->ny, pos, d) < 0)
+        return fail(c, "direction sampling exceeded 64 attempts");
+      emitted += tot;
+      int64_t cr = or_trace_packet(c, pos, d, N, &escaped, &absorbed, 0, NULL, NULL, NULL);
+      if (cr < 0) return -1;
+      crossings += cr;
+      ++traced;
+    }
+  }
   c->budget[0] = emitted; c->budget[1] = absorbed; c->budget[2] = escaped;
   c->budget[3] = crossings; c->budget[4] = traced;
 
@@ -644,10 +738,16 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
       ch.G_HeII = NHeII > 0 ? ((double)c->dHeII[i] * q) / (dt * NHeII) : 0.0;
       int64_t nabs = (c->dHI[i] + c->dHeI[i]) + c->dHeII[i];
       ch.heat_per_ion = nabs > 0 ? ((double)c->dE[i] * qE) / ((double)nabs * q) : 0.0;
-      ch.isothermal = c->isothermal; ch.caseB = c->caseB; ch.T_cmb = c->T_cmb;
+      /* with the diffuse field on, recombinations to the ground state are
+         no longer absorbed on the spot: case A, and they are counted */
+      ch.isothermal = c->isothermal; ch.caseB = c->f_rec > 0 ? 0 : c->caseB; ch.T_cmb = c->T_cmb;
       ch.eps = c->chem_eps; ch.max_sub = c->chem_max_sub; ch.cool_mask = c->cool_mask;
+      ch.count_rec = c->f_rec > 0;
+      ch.rec[0] = ch.rec[1] = ch.rec[2] = 0.0;
       subs += or_chem_cell(&ch, dt);
       c->xHII[i] = ch.xHII; c->xHeII[i] = ch.xHeII; c->xHeIII[i] = ch.xHeIII; c->T[i] = ch.T;
+      if (ch.count_rec)
+        for (int a = 0; a < 3; ++a) c->rec[a][i] += ch.rec[a] * V;
     }
     c->budget[7] = subs;
   }
@@ -669,6 +769,9 @@ int oracle_read_fields(or_ctx* c, int f, void* out) {
     case OR_F_DEP_E: memcpy(out, c->dE, n * 8); return 0;
     case OR_F_BUDGET: memcpy(out, c->budget, sizeof c->budget); return 0;
     case OR_F_NH: memcpy(out, c->nH, n * 8); return 0;
+    case OR_F_REC_HI: memcpy(out, c->rec[0], n * 8); return 0;
+    case OR_F_REC_HEI: memcpy(out, c->rec[1], n * 8); return 0;
+    case OR_F_REC_HEII: memcpy(out, c->rec[2], n * 8); return 0;
     default: return fail(c, "unknown field id");
   }
 }
@@ -681,6 +784,9 @@ int oracle_write_fields(or_ctx* c, int f, const void* in) {
     case OR_F_XHEII: memcpy(c->xHeII, in, n * 8); return 0;
     case OR_F_XHEIII: memcpy(c->xHeIII, in, n * 8); return 0;
     case OR_F_T: memcpy(c->T, in, n * 8); return 0;
+    case OR_F_REC_HI: memcpy(c->rec[0], in, n * 8); return 0;
+    case OR_F_REC_HEI: memcpy(c->rec[1], in, n * 8); return 0;
+    case OR_F_REC_HEII: memcpy(c->rec[2], in, n * 8); return 0;
     default: return fail(c, "field is not writable");
   }
 }

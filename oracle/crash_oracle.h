@@ -24,7 +24,10 @@ enum {
   OR_F_XHII = 0, OR_F_XHEII = 1, OR_F_XHEIII = 2, OR_F_T = 3,   /* f64 per cell */
   OR_F_DEP_HI = 4, OR_F_DEP_HEI = 5, OR_F_DEP_HEII = 6, OR_F_DEP_E = 7, /* i64 per cell */
   OR_F_BUDGET = 8,                                              /* i64[8] */
-  OR_F_NH = 9                                                   /* f64 per cell (read only) */
+  OR_F_NH = 9,                                                  /* f64 per cell (read only) */
+  /* f64 per cell (r/w): photons of recombinations to the ground state of
+     H I, He I and He II waiting for re-emission (diffuse field on) */
+  OR_F_REC_HI = 11, OR_F_REC_HEI = 12, OR_F_REC_HEII = 13
 };
 
 typedef struct {
@@ -38,6 +41,8 @@ typedef struct {
   int isothermal, caseB;
   double z_compton;              /* < 0: Compton term off */
   uint64_t seed;
+  double f_rec;                  /* > 0: diffuse recombination radiation with this
+                                    re-emission threshold (Sec. 2); 0: off */
 } or_grid_desc;
 
 typedef struct or_ctx or_ctx;
@@ -67,6 +72,10 @@ int64_t or_trace_packet(or_ctx* c, const double pos[3], const double dir[3],
                         int64_t* content, int64_t* escaped, int64_t* absorbed,
                         int max_log, int64_t* log_cell, double* log_len, int* n_log);
 int or_freeze_absorbers(or_ctx* c);   /* absorbers from the current state; zero deposits */
+/* start of the re-emission packet of cell `cell` at step `step` (grid units,
+   inside the cell) and its direction; returns the direction attempts used */
+int or_rec_start(uint64_t seed, uint32_t step, int64_t cell, int nx, int ny, double pos[3],
+                 double dir[3]);
 
 /* one cell of the ionisation network + temperature over dt (Sec. 2, Sec. 3.2) */
 typedef struct {
@@ -79,6 +88,9 @@ typedef struct {
   double eps;                       /* relative change allowed per sub-step */
   int max_sub;
   int cool_mask;                    /* OR_C_* bits of processes switched on */
+  int count_rec;                    /* 1: count recombinations to the ground state */
+  double rec[3];                    /* out (added to): such recombinations per cm^3 into
+                                       H I, He I, He II over dt */
 } or_chem_t;
 
 enum {

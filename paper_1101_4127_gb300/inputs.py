@@ -141,6 +141,7 @@ class Box:
     bin_eV: np.ndarray          # (n_bins,)
     bin_frac: np.ndarray        # (n_src, n_bins)
     dims: Optional[tuple] = None  # (nx, ny, nz) for non-cubic grids; default (n, n, n)
+    f_rec: float = 0.0            # > 0: diffuse recombination field with this threshold
 
     @property
     def n_src(self) -> int:
@@ -182,6 +183,24 @@ def stromgren_32(n: int = 32) -> Workload:
               src_pos=np.zeros((1, 3)), src_ndot=np.array([5e48]),
               bin_eV=bE, bin_frac=bf)
     return Workload("stromgren_32^3_H_1src_1bin", [box], [100_000], 20,
+                    0.5 * MYR_S, "fp64")
+
+
+def stromgren_rec(n: int = 128, packets: int = 1_000_000, steps: int = 20,
+                  f_rec: float = 0.1) -> Workload:
+    """Test-1-like Stroemgren sphere with the diffuse recombination field
+    (Sec. 4.2.1): isothermal pure H, n_H = 1e-3, T = 1e4 K, x_HII0 = 1.2e-3,
+    corner source of 5e48 photons/s at 13.6 eV in a 6.6 kpc box of n^3 cells;
+    case A recombination, a cell re-emits once 10% of its atoms have
+    recombined to the ground state; steps of 0.5 Myr."""
+    E = np.array([13.6])
+    bE, bf = _bins_for(1, E, np.array([1.0]))
+    box = Box(n=n, box_cm=6.6 * KPC_CM, nH=None, nH0=1e-3, he_over_h=0.0,
+              x_HII0=1.2e-3, x_HeII0=0.0, x_HeIII0=0.0, T0=1e4,
+              isothermal=1, caseB=0, z_compton=-1.0, seed=SEED_BASE + 7,
+              src_pos=np.zeros((1, 3)), src_ndot=np.array([5e48]),
+              bin_eV=bE, bin_frac=bf, f_rec=f_rec)
+    return Workload(f"stromgren_rec_{n}^3_H_1src_1bin_frec{f_rec:g}", [box], [packets], steps,
                     0.5 * MYR_S, "fp64")
 
 

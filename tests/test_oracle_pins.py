@@ -481,3 +481,122 @@ def test_step_converts_deposits_to_ionisations_and_heat():
     heat = g.read(oracle.F_DEP_E).sum() * 2.0 ** (b[5] + b[6]) * 1.602176634e-12
     assert n1 - n0 == pytest.approx(b[1] * q, rel=0.005)
     assert e1 - e0 == pytest.approx(heat, rel=0.005)
+
+
+# ------------------------------------------------ diffuse recombination field
+def test_ground_state_recombinations_are_the_case_a_minus_b_share():
+    """Pure recombination at fixed T (no collisional ionisation): every H II
+    recombination lowers x, so
+    the recombinations over dt are n_H (x0 - x1) exactly (backward Euler
+    keeps this identity sub-step by sub-step), and those to the ground state
+    are the share (alpha_A - alpha_B) / alpha_A of them."""
+    T = 1e4
+    rA, rB = oracle.rates(T, 0), oracle.rates(T, 1)
+    for x0, dt in [(0.9, 1e13), (0.5, 3e14), (0.999, 2e15)]:
+        st, n = oracle.chem_cell(dt, nH=1e-3, xHII=x0, T=T, caseB=0, isothermal=1,
+                                 count_rec=1, eps=0.01,
+                                 cool_mask=oracle.C_ALL & ~oracle.C_COLL_ION)
+        total = 1e-3 * (x0 - st["xHII"])
+        want = (rA[0] - rB[0]) / rA[0] * total
+        assert n > 1
+        assert st["rec"][0] == pytest.approx(want, rel=1e-9)
+        assert st["rec"][1] == 0.0 and st["rec"][2] == 0.0
+
+
+def test_helium_ground_state_recombinations_follow_the_chain():
+    """He III -> He II -> He I with radiative recombination only: the He III
+    recombinations are n_He (y3_0 - y3_1), the He II ones n_He (y1_1 - y1_0);
+    the ground-state shares of each use that ion's case A and B rates."""
+    T = 2e4
+    rA, rB = oracle.rates(T, 0), oracle.rates(T, 1)
+    nH, nHe = 1e-3, 8e-5
+    mask = oracle.C_ALL & ~oracle.C_DIELEC & ~oracle.C_COLL_ION
+    st, _ = oracle.chem_cell(5e14, nH=nH, nHe=nHe, xHII=1.0, xHeII=0.3, xHeIII=0.6, T=T,
+                             caseB=0, isothermal=1, count_rec=1, eps=0.01, cool_mask=mask)
+    y1_0, y1_1 = 1.0 - 0.3 - 0.6, 1.0 - st["xHeII"] - st["xHeIII"]
+    assert st["rec"][2] == pytest.approx((rA[2] - rB[2]) / rA[2] * nHe * (0.6 - st["xHeIII"]), rel=1e-8)
+    assert st["rec"][1] == pytest.approx((rA[1] - rB[1]) / rA[1] * nHe * (y1_1 - y1_0), rel=1e-8)
+
+
+def _rec_grid(n=6, f_rec=0.1, xHII0=1.0, bins=(13.6,), seed=11, he=0.0):
+    dl = 3.086e21
+    g = oracle.OracleGrid(n, n, n, n * dl, n_H0=1e-3, he_over_h=he, x_HII0=xHII0,
+                          x_HeII0=0.0 if he == 0 else 1.0, T0=1e4, isothermal=1, caseB=0,
+                          seed=seed, f_rec=f_rec)
+    E = np.array(bins, float)
+    g.add_sources([[0.5, 0.5, 0.5]], [1e48], E, np.full(len(E), 1.0 / len(E)))
+    g.set_options(chemistry=0)
+    return g, dl ** 3
+
+
+def test_reemission_sends_the_count_in_step_quanta_and_resets_it():
+    """A cell over the threshold re-emits its ground-state recombinations as
+    one packet of llrint(count / q) quanta (q = 2^E, two bits of headroom
+    above the sources' quantum) and its count restarts at 0; a cell below
+    the threshold keeps its count; in a transparent grid everything escapes."""
+    dt, P = 3e13, 64
+    ref, V = _rec_grid()
+    ref.step(dt, P)
+    b0 = ref.read(oracle.F_BUDGET)
+    g, V = _rec_grid()
+    atoms = 1e-3 * V
+    rec = np.zeros(g.ncell)
+    rec[100] = 0.25 * atoms          # above f_rec = 0.1
+    rec[7] = 0.05 * atoms            # below
+    g.write(oracle.F_REC_HI, rec)
+    g.step(dt, P)
+    b = g.read(oracle.F_BUDGET)
+    E = int(b[5])
+    assert E == math.ceil(math.log2(1e48 * dt)) - 62 + 2
+    quanta = round(rec[100] / 2.0 ** E)
+    assert b[0] - b0[0] == quanta and b[4] == b0[4] + 1
+    assert b[0] == b[1] + b[2] and b[1] == 0
+    after = g.read(oracle.F_REC_HI).reshape(-1)
+    assert after[100] == 0.0 and after[7] == rec[7]
+
+
+def test_reemitted_photons_take_the_lowest_bin_above_threshold():
+    """He II -> He I photons (>= 24.6 eV) are absorbed only through the bin at
+    or above 24.6 eV: with bins (13.6, 30, 60) eV and neutral helium as the
+    only absorber, they deposit into He I; with bins (13.6, 20) they have no
+    bin and are not emitted, though the count is reset."""
+    dt, P = 3e13, 8
+    for bins, emits in [((13.6, 30.0, 60.0), True), ((13.6, 20.0), False)]:
+        ref, V = _rec_grid(bins=bins, he=0.1, xHII0=1.0)
+        ref.step(dt, P)
+        g, V = _rec_grid(bins=bins, he=0.1, xHII0=1.0)
+        rec = np.zeros(g.ncell)
+        rec[50] = 0.5 * 1e-4 * V
+        g.write(oracle.F_REC_HEI, rec)
+        g.step(dt, P)
+        extra = g.read(oracle.F_BUDGET)[0] - ref.read(oracle.F_BUDGET)[0]
+        assert (extra > 0) == emits
+        assert g.read(oracle.F_REC_HEI).reshape(-1)[50] == 0.0
+
+
+def test_reemission_starts_inside_its_cell_uniformly():
+    n = 7
+    offs = []
+    for cell in range(0, n ** 3, 3):
+        pos, d, k = oracle.rec_start(99, 4, cell, n, n)
+        ijk = (cell % n, (cell // n) % n, cell // (n * n))
+        assert tuple(int(math.floor(p)) for p in pos) == ijk
+        assert abs(np.linalg.norm(d) - 1.0) < 1e-12 and k >= 1
+        offs.append(pos - np.array(ijk))
+    offs = np.array(offs)
+    assert np.all(np.abs(offs.mean(axis=0) - 0.5) < 0.05)
+    assert np.all(np.abs(offs.var(axis=0) - 1 / 12) < 0.02)
+
+
+def test_budget_closes_with_reemission_in_an_absorbing_medium():
+    dt, P = 3e13, 200
+    g, V = _rec_grid(n=8, xHII0=0.5)
+    rng = np.random.default_rng(3)
+    rec = rng.uniform(0.0, 0.3, g.ncell) * 1e-3 * V
+    g.write(oracle.F_REC_HI, rec)
+    g.set_options(chemistry=1)
+    for _ in range(3):
+        g.step(dt, P)
+        b = g.read(oracle.F_BUDGET)
+        assert b[0] == b[1] + b[2]
+        assert b[4] > P
