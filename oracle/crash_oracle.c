@@ -514,6 +514,7 @@ int or_chem_cell(or_chem_t* c, double dt) {
   double r[17], rB[17];
   while (rem > 0) {
     or_rates(T, c->caseB, r);
+    if (c->count_rec) or_rates(T, 1, rB);     /* case B at the same temperature */
     double aH = use_rec ? r[0] : 0.0, aHe2 = use_rec ? r[1] + ((mask & OR_C_DIELEC) ? r[3] : 0.0) : 0.0;
     double aHe3 = use_rec ? r[2] : 0.0;
     double bH = use_coll ? r[4] : 0.0, bHe1 = use_coll ? r[5] : 0.0, bHe2 = use_coll ? r[6] : 0.0;
@@ -594,9 +595,9 @@ int or_chem_cell(or_chem_t* c, double dt) {
     }
     if (c->count_rec && use_rec) {
       /* recombinations straight to the ground state, alpha_A - alpha_B of
-         each ion (at least 0), with n_e and the ions at the end of the
-         sub-step as in the backward-Euler update */
-      or_rates(T, 1, rB);
+         each ion (at least 0) at the sub-step's starting temperature, with
+         n_e and the ions at the end of the sub-step as in the backward-Euler
+         update */
       double gH = r[0] - rB[0], g2 = r[1] - rB[1], g3 = r[2] - rB[2];
       if (gH < 0.0) gH = 0.0;
       if (g2 < 0.0) g2 = 0.0;
