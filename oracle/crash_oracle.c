@@ -633,9 +633,26 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
   for (int s = 0; s < c->n_src; ++s) if (c->ndot[s] > mx) mx = c->ndot[s];
   double X = ((double)c->n_src * mx) * dt;
   int E = X > 0 ? ceil_log2(X) - 62 : 0;
-  /* with the diffuse field on, two more bits of room for the re-emitted
-     photons (a step re-emits at most what earlier steps absorbed) */
-  if (c->f_rec > 0) E += 2;
+  if (c->f_rec > 0) {
+    /* the diffuse field re-emits this step at most ncell times the largest
+       count over its threshold: the quantum also keeps that below 2^62, and
+       one more bit keeps sources plus re-emission below 2^62 */
+    const double V = (c->dl * c->dl) * c->dl;
+    double rmax = 0.0;
+    for (int64_t i = 0; i < c->ncell; ++i) {
+      const double atoms[3] = {c->nH[i] * V, c->nH[i] * c->he_over_h * V,
+                               c->nH[i] * c->he_over_h * V};
+      for (int a = 0; a < 3; ++a) {
+        const double v = c->rec[a][i];
+        if (atoms[a] > 0 && v > 0 && v >= c->f_rec * atoms[a] && v > rmax) rmax = v;
+      }
+    }
+    if (rmax > 0) {
+      const int Er = ceil_log2(rmax * (double)c->ncell) - 62;
+      if (Er > E) E = Er;
+    }
+    E += 1;
+  }
   c->budget[5] = E;
   c->budget[6] = c->heatF;
 

@@ -531,13 +531,11 @@ def _rec_grid(n=6, f_rec=0.1, xHII0=1.0, bins=(13.6,), seed=11, he=0.0):
 
 def test_reemission_sends_the_count_in_step_quanta_and_resets_it():
     """A cell over the threshold re-emits its ground-state recombinations as
-    one packet of llrint(count / q) quanta (q = 2^E, two bits of headroom
-    above the sources' quantum) and its count restarts at 0; a cell below
-    the threshold keeps its count; in a transparent grid everything escapes."""
+    one packet of llrint(count / q) quanta and its count restarts at 0; a
+    cell below the threshold keeps its count; in a transparent grid
+    everything escapes.  q = 2^E keeps both the sources' photons and ncell
+    times the largest count over threshold below 2^61 quanta."""
     dt, P = 3e13, 64
-    ref, V = _rec_grid()
-    ref.step(dt, P)
-    b0 = ref.read(oracle.F_BUDGET)
     g, V = _rec_grid()
     atoms = 1e-3 * V
     rec = np.zeros(g.ncell)
@@ -547,30 +545,34 @@ def test_reemission_sends_the_count_in_step_quanta_and_resets_it():
     g.step(dt, P)
     b = g.read(oracle.F_BUDGET)
     E = int(b[5])
-    assert E == math.ceil(math.log2(1e48 * dt)) - 62 + 2
+    E_src = math.ceil(math.log2(1e48 * dt)) - 62
+    E_rec = math.ceil(math.log2(rec[100] * g.ncell)) - 62
+    assert E == max(E_src, E_rec) + 1
+    source_quanta = round(math.ldexp(1e48 * dt, -E))
     quanta = round(rec[100] / 2.0 ** E)
-    assert b[0] - b0[0] == quanta and b[4] == b0[4] + 1
+    assert b[0] == source_quanta + quanta and b[4] == P + 1
     assert b[0] == b[1] + b[2] and b[1] == 0
     after = g.read(oracle.F_REC_HI).reshape(-1)
     assert after[100] == 0.0 and after[7] == rec[7]
 
 
 def test_reemitted_photons_take_the_lowest_bin_above_threshold():
-    """He II -> He I photons (>= 24.6 eV) are absorbed only through the bin at
-    or above 24.6 eV: with bins (13.6, 30, 60) eV and neutral helium as the
-    only absorber, they deposit into He I; with bins (13.6, 20) they have no
-    bin and are not emitted, though the count is reset."""
+    """He II -> He I photons (>= 24.6 eV) go to the lowest bin at or above
+    24.6 eV: with bins (13.6, 30, 60) eV one packet leaves carrying the count
+    in quanta; with bins (13.6, 20) eV there is no such bin, no packet leaves
+    and the count is reset all the same."""
     dt, P = 3e13, 8
     for bins, emits in [((13.6, 30.0, 60.0), True), ((13.6, 20.0), False)]:
-        ref, V = _rec_grid(bins=bins, he=0.1, xHII0=1.0)
-        ref.step(dt, P)
         g, V = _rec_grid(bins=bins, he=0.1, xHII0=1.0)
         rec = np.zeros(g.ncell)
         rec[50] = 0.5 * 1e-4 * V
         g.write(oracle.F_REC_HEI, rec)
         g.step(dt, P)
-        extra = g.read(oracle.F_BUDGET)[0] - ref.read(oracle.F_BUDGET)[0]
-        assert (extra > 0) == emits
+        b = g.read(oracle.F_BUDGET)
+        E = int(b[5])
+        extra = int(b[0]) - round(math.ldexp(1e48 * dt, -E))
+        assert b[4] == P + (1 if emits else 0)
+        assert extra == (round(rec[50] / 2.0 ** E) if emits else 0)
         assert g.read(oracle.F_REC_HEI).reshape(-1)[50] == 0.0
 
 
@@ -600,3 +602,17 @@ def test_budget_closes_with_reemission_in_an_absorbing_medium():
         b = g.read(oracle.F_BUDGET)
         assert b[0] == b[1] + b[2]
         assert b[4] > P
+
+
+def test_reemission_far_from_equilibrium_keeps_the_budget_exact():
+    """A dense, mostly ionised grid recombines tens of times more photons
+    per step than its source emits; the quantum grows with the largest
+    count over threshold, so the int64 budget stays exact and positive."""
+    dl = 6.6 * inputs.KPC_CM / 16
+    g = oracle.OracleGrid(16, 16, 16, 16 * dl, n_H0=1e-2, x_HII0=0.9, T0=1e4, isothermal=1,
+                          caseB=0, seed=3, f_rec=0.1)
+    g.add_sources([[8.3, 7.8, 8.1]], [5e48], np.array([13.6]), np.array([1.0]))
+    for _ in range(5):
+        g.step(5.0 * inputs.MYR_S, 20000)
+        b = g.read(oracle.F_BUDGET)
+        assert b[0] > 0 and b[1] >= 0 and b[2] >= 0 and b[0] == b[1] + b[2]
