@@ -57,6 +57,10 @@ def workload(name):
         return inputs.lognormal_512(n=256, n_src=2000, packets=4_000_000, thin=True), native.CRASH_MIXED
     if name == "lognormal_512_thin":
         return inputs.lognormal_512(thin=True), native.CRASH_MIXED
+    if name == "stromgren_rec_128":      # diffuse recombination field (Test 1 set-up)
+        return inputs.stromgren_rec(n=128, packets=10_000_000), native.CRASH_MIXED
+    if name == "stromgren_rec_128_fp64":
+        return inputs.stromgren_rec(n=128, packets=10_000_000), native.CRASH_FP64_PLAIN
     if name == "lognormal_512_neutral":
         return inputs.lognormal_512(thin=False), native.CRASH_MIXED
     raise SystemExit(f"unknown workload {name}")
@@ -476,6 +480,12 @@ def run_crash(args):
             "transport_ms_per_step": kms / args.steps,
             "chem_substeps_per_cell": float(tot1[7] - tot0[7]) / (args.steps * ncell_all),
         }
+        if any(getattr(bx, "f_rec", 0.0) > 0 for bx in boxes):
+            # diffuse recombination field: re-emission packets traced per step
+            # beyond the sources' packets
+            line["config"]["f_rec"] = max(getattr(bx, "f_rec", 0.0) for bx in boxes)
+            line["reemitted_packets_per_step"] = (float(tot1[4] - tot0[4]) / args.steps
+                                                  - float(sum(Plist)))
         print(json.dumps(line), flush=True)
     if g is not None:
         g.close()

@@ -61,8 +61,12 @@ typedef enum {
                                packets traced, quantum exponent E, heat exponent F,
                                chemistry sub-steps (all for the last step) */
   CRASH_F_NH = 9,           /* double per cell: n_H (read only) */
-  CRASH_F_TOTALS = 10       /* int64[8]: slots 0-4 and 7 of CRASH_F_BUDGET summed over all
+  CRASH_F_TOTALS = 10,      /* int64[8]: slots 0-4 and 7 of CRASH_F_BUDGET summed over all
                                steps since the context was created (slots 5, 6: last step) */
+  /* double per cell (r/w), only when the diffuse field is on (f_rec > 0):
+     photons of recombinations to the ground state of H I, He I and He II
+     counted since the cell last re-emitted them */
+  CRASH_F_REC_HI = 11, CRASH_F_REC_HEI = 12, CRASH_F_REC_HEII = 13
 } crash_field;
 
 /* One grid and its initial state.  Section 2 of the paper: a static H/He
@@ -81,6 +85,15 @@ typedef struct {
   double z_compton;          /* redshift of the CMB for Compton exchange; < 0 => off */
   uint64_t seed;             /* Philox key of this grid */
   int precision;             /* crash_precision; must be equal for all boxes of a batch */
+  double f_rec;              /* diffuse recombination radiation (Sec. 2): 0 => off (on-the-spot
+                                recombination as caseB says).  > 0 => case A recombination;
+                                recombinations to the ground state are counted per cell and
+                                species, and at the start of a step every cell where a
+                                species' count reached f_rec times that element's atoms in
+                                the cell re-emits it as one isotropic packet from a uniform
+                                point of the cell, in the lowest bin at or above the
+                                species' threshold; the count then restarts.  The photon
+                                quantum of the step gets two bits of headroom. */
 } crash_grid_desc;
 
 /* Run options (crash_default_opts fills the defaults). */
@@ -211,7 +224,8 @@ const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error
    device array that every GPU loading the library holds until the process
    exits.
      grid: host struct; nx, ny, nz, box_cm, he_over_h, isothermal, caseB and
-       seed are used, the per-cell pointers are ignored.
+       seed are used, the per-cell pointers are ignored; f_rec must be 0
+       (source packets only: CRASH_ERR_ARG otherwise).
      pos_cells, ndot, bin_eV, bin_frac: host arrays as in crash_add_sources;
        1 <= n_src <= CRASH_NOALLOC_MAX_SOURCES (larger counts are rejected
        with CRASH_ERR_OVERFLOW), 1 <= n_bins <= 16.

@@ -53,6 +53,14 @@ struct crash_ctx {
   int* src_cell = nullptr;
   int64_t *src_base = nullptr, *src_rem = nullptr;
   int n_src_total = 0, src_cap = 0;
+  // diffuse recombination field (some box has f_rec > 0)
+  bool any_rec = false;
+  double* rec = nullptr;            // [3][cells]
+  long long* rec_list = nullptr;    // [cells][4]
+  unsigned* rec_count = nullptr;
+  unsigned long long* rec_rmax = nullptr;   // [n_boxes]
+  double* snap_rec = nullptr;       // checkpoint copy of rec
+  int rec_bin[3] = {-1, -1, -1};
   // bins
   int n_bins = 0;
   std::vector<double> bin_eV;
@@ -134,7 +142,7 @@ static void release(crash_ctx* c) {
   void* ptrs[] = {c->nH, c->xHII, c->xHeII, c->xHeIII, c->T, c->abs64, c->abs32, c->dep,
                   c->d_meta, c->budget, c->totals, c->step_dev, c->work, c->err, c->boxE, c->src_pos, c->src_ndot,
                   c->src_frac, c->src_base, c->src_rem, c->src_pos32, c->src_cell, c->snap,
-                  c->snap_step};
+                  c->snap_step, c->rec, c->rec_list, c->rec_count, c->rec_rmax, c->snap_rec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -172,6 +180,7 @@ static crash_status validate_desc(const crash_grid_desc& d, int i) {
   if ((int64_t)d.nx * d.ny * d.nz > ((int64_t)1 << 40))
     return set_err(c, CRASH_ERR_OVERFLOW, "grid too large");
   if (!d.T && !(d.T0 > 0)) return set_err(c, CRASH_ERR_ARG, "T0 must be positive");
+  if (!(d.f_rec >= 0 && d.f_rec <= 1)) return set_err(c, CRASH_ERR_ARG, "f_rec must be in [0, 1]");
   return CRASH_OK;
 }
 
@@ -242,6 +251,8 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
     m.seed = d.seed;
     m.caseB = d.caseB ? 1 : 0;
     m.max_iter = d.nx + d.ny + d.nz + 3;
+    m.f_rec = d.f_rec;
+    c->any_rec |= d.f_rec > 0;
     off += m.ncell;
     c->any_he |= d.he_over_h > 0;
     c->any_heat |= !d.isothermal;
@@ -303,6 +314,12 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
       {(void**)&c->err, sizeof(int)}, {(void**)&c->boxE, sizeof(int) * n_boxes}};
   if (c->precision == CRASH_MIXED) allocs.push_back({(void**)&c->abs32, n * 16});
   else allocs.push_back({(void**)&c->abs64, n * 32});
+  if (c->any_rec) {
+    allocs.push_back({(void**)&c->rec, n * 24});
+    allocs.push_back({(void**)&c->rec_list, n * 32});
+    allocs.push_back({(void**)&c->rec_count, 16});
+    allocs.push_back({(void**)&c->rec_rmax, 8 * (size_t)n_boxes});
+  }
   {
     size_t want = 0;
     for (auto& a : allocs) want += a.bytes;
@@ -326,6 +343,7 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
   cudaMemset(c->step_dev, 0, 8);
   cudaMemset(c->err, 0, sizeof(int));
   cudaMemset(c->dep, 0, n * 32);
+  if (c->any_rec) cudaMemset(c->rec, 0, n * 24);
   for (int i = 0; i < n_boxes; ++i) {
     crash_status st = upload_box_state(c, i);
     if (st != CRASH_OK) {
@@ -469,6 +487,15 @@ extern "C" crash_status crash_add_sources_box(crash_ctx* c, int box, int n_src,
   c->bin_eV.assign(bin_eV, bin_eV + n_bins);
   int heatF = 0;
   cross_sections(n_bins, bin_eV, c->tables, heatF);
+  // re-emitted photons of H I, He I, He II: the lowest bin at or above the
+  // species' ionisation threshold (-1 when there is none)
+  const double Eth[3] = {13.6, 24.6, 54.4};
+  for (int sp = 0; sp < 3; ++sp) {
+    c->rec_bin[sp] = -1;
+    for (int j = 0; j < n_bins; ++j)
+      if (bin_eV[j] >= Eth[sp] && (c->rec_bin[sp] < 0 || bin_eV[j] < bin_eV[c->rec_bin[sp]]))
+        c->rec_bin[sp] = j;
+  }
   for (int b = 0; b < c->n_boxes; ++b) c->meta[b].heatF = heatF;
   c->meta[box].ndot_max = mx;
   crash_status st = rebuild_sources(c);
@@ -509,6 +536,10 @@ extern "C" crash_status crash_checkpoint(crash_ctx* c, int op) {
     for (int i = 0; i < 4; ++i)
       CK(cudaMemcpyAsync(c->snap + i * n, f[i], n * 8, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(c->snap_step, c->step_dev, 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->any_rec) {
+      if (!c->snap_rec) CK(cudaMalloc(&c->snap_rec, n * 24));
+      CK(cudaMemcpyAsync(c->snap_rec, c->rec, n * 24, cudaMemcpyDeviceToDevice, c->stream));
+    }
     return CRASH_OK;
   }
   if (op != CRASH_CKPT_RESTORE_STATE && op != CRASH_CKPT_RESTORE)
@@ -516,6 +547,8 @@ extern "C" crash_status crash_checkpoint(crash_ctx* c, int op) {
   if (!c->snap) return set_err(c, CRASH_ERR_STATE, "no checkpoint saved");
   for (int i = 0; i < 4; ++i)
     CK(cudaMemcpyAsync(f[i], c->snap + i * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->any_rec && c->snap_rec)
+    CK(cudaMemcpyAsync(c->rec, c->snap_rec, n * 24, cudaMemcpyDeviceToDevice, c->stream));
   if (op == CRASH_CKPT_RESTORE)
     CK(cudaMemcpyAsync(c->step_dev, c->snap_step, 8, cudaMemcpyDeviceToDevice, c->stream));
   return CRASH_OK;
@@ -571,6 +604,12 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
   a.chem_eps = c->opts.chem_eps;
   a.chem_max_sub = c->opts.chem_max_sub;
   a.cool_mask = c->opts.cool_mask;
+  a.any_rec = c->any_rec ? 1 : 0;
+  a.rec = c->rec;
+  a.rec_list = c->rec_list;
+  a.rec_count = c->rec_count;
+  a.rec_rmax = c->rec_rmax;
+  for (int sp = 0; sp < 3; ++sp) a.rec_bin[sp] = c->rec_bin[sp];
   return a;
 }
 
@@ -578,8 +617,15 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
 static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, int64_t* nk) {
   CK(cudaMemsetAsync(c->budget, 0, 64 * (size_t)c->n_boxes, c->stream));
   launch_prep(a, c->precision, c->stream);
+  if (c->any_rec) launch_rec_max(a, c->stream);      // the quantum covers the re-emission
   launch_budget(a, c->tables, c->stream);
   *nk = 3 + (c->opts.chemistry ? 1 : 0);   // prep, budget, end-of-step, chemistry
+  // diffuse recombination field: this step's re-emitting cells (from the
+  // counts of earlier steps), traced after the source packets
+  if (c->any_rec) {
+    launch_rec_select(a, c->stream);
+    *nk += 2;
+  }
   if (c->precision == CRASH_MIXED) {
     int rc = launch_trace_mixed(a, c->tables, c->opts, c->wf, c->max_iter, c->stream,
                                 timing ? &c->events : nullptr, &c->ev_used);
@@ -601,6 +647,15 @@ static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, i
       CK(cudaEventRecord(c->events[c->ev_used].second, c->stream));
       c->ev_used++;
     }
+  }
+  if (c->any_rec) {
+    if (c->precision == CRASH_MIXED) {
+      if (launch_rec_mixed(a, c->tables, c->stream) < 0)
+        return set_err(c, CRASH_ERR_CUDA, "re-emission launch failed");
+    } else {
+      launch_rec_fp64(a, c->tables, c->stream);
+    }
+    *nk += 1;
   }
   if (c->opts.chemistry) launch_chemistry(a, c->stream);
   k_end_step<<<(8 * c->n_boxes + 255) / 256, 256, 0, c->stream>>>(c->step_dev, c->budget,
@@ -742,6 +797,11 @@ extern "C" crash_status crash_read_fields_box(crash_ctx* c, int box, int f, void
       break;
     case CRASH_F_BUDGET: CK(cudaMemcpy(out, c->budget + 8 * box, 64, cudaMemcpyDeviceToHost)); break;
     case CRASH_F_TOTALS: CK(cudaMemcpy(out, c->totals + 8 * box, 64, cudaMemcpyDeviceToHost)); break;
+    case CRASH_F_REC_HI: case CRASH_F_REC_HEI: case CRASH_F_REC_HEII:
+      if (!c->rec) return set_err(c, CRASH_ERR_STATE, "the diffuse recombination field is off (f_rec = 0)");
+      CK(cudaMemcpy(out, c->rec + (size_t)(f - CRASH_F_REC_HI) * c->n_cells + m.cell_off, n * 8,
+                    cudaMemcpyDeviceToHost));
+      break;
     case CRASH_F_NH: {
       std::vector<float> tmp(n);
       CK(cudaMemcpy(tmp.data(), c->nH + m.cell_off, n * 4, cudaMemcpyDeviceToHost));
@@ -772,6 +832,10 @@ extern "C" crash_status crash_write_fields_box(crash_ctx* c, int box, int f, con
     case CRASH_F_XHEII: dst = c->xHeII; break;
     case CRASH_F_XHEIII: dst = c->xHeIII; break;
     case CRASH_F_T: dst = c->T; break;
+    case CRASH_F_REC_HI: case CRASH_F_REC_HEI: case CRASH_F_REC_HEII:
+      if (!c->rec) return set_err(c, CRASH_ERR_STATE, "the diffuse recombination field is off (f_rec = 0)");
+      dst = c->rec + (size_t)(f - CRASH_F_REC_HI) * c->n_cells;
+      break;
     default: return set_err(c, CRASH_ERR_ARG, "field is not writable");
   }
   CK(cudaMemcpy(dst + m.cell_off, in, n * 8, cudaMemcpyHostToDevice));

@@ -49,6 +49,7 @@ struct BoxMeta {
   int64_t tile_off;
   int tile_bits;
   int max_iter;            // nx + ny + nz + 3: bound on DDA steps of one packet
+  double f_rec;            // > 0: diffuse recombination field with this re-emission threshold
 };
 
 // Cross sections and heating weights per species and bin (passed by value;
@@ -99,6 +100,13 @@ struct StepArgs {
   double chem_eps;
   int chem_max_sub;
   int cool_mask;
+  // diffuse recombination field (some box has f_rec > 0)
+  int any_rec;
+  double* rec;               // [3][cells] ground-state recombination photons (H I, He I, He II)
+  long long* rec_list;       // [cells][4] re-emitting cell, then quanta of H I, He I, He II photons
+  unsigned* rec_count;       // entries of rec_list this step
+  unsigned long long* rec_rmax;  // [n_boxes] bits of the largest count over threshold (>= 0 doubles)
+  int rec_bin[3];            // bin of each species' re-emitted photons, -1 => none
 };
 
 // device error bits
@@ -109,6 +117,12 @@ void launch_prep(const StepArgs& a, int precision, cudaStream_t s);
 void launch_budget(const StepArgs& a, const BinTables& t, cudaStream_t s);
 void launch_trace_fp64(const StepArgs& a, const BinTables& t, int block, cudaStream_t s);
 void launch_chemistry(const StepArgs& a, cudaStream_t s);
+// diffuse recombination field: pick this step's re-emitting cells (and
+// restart their counts), then trace one packet per cell in either form
+void launch_rec_max(const StepArgs& a, cudaStream_t s);   // before launch_budget
+void launch_rec_select(const StepArgs& a, cudaStream_t s);
+void launch_rec_fp64(const StepArgs& a, const BinTables& t, cudaStream_t s);
+int launch_rec_mixed(const StepArgs& a, const BinTables& t, cudaStream_t s);
 
 // Mixed-form transport.  Returns the number of kernels launched (>= 0) or
 // -1 on a launch error.  ev/ev_used: optional event pairs recorded around

@@ -111,18 +111,30 @@ __device__ __forceinline__ double cooling_rate(const Rates& r, int mask, double 
 }
 
 struct CellIn {
-  double nH, nHe, GH, G1, G2, eps_heat, Tcmb, ccomp, eps;
-  int iso, caseB, mask, max_sub;
+  double nH, nHe, GH, G1, G2, eps_heat, Tcmb, ccomp, eps, V;
+  int iso, caseB, mask, max_sub, count_rec;
 };
 
 // One sub-step of the cell integration; updates x (HII), y2 (HeII), y3
-// (HeIII), T and the remaining time rem (0 after the last sub-step).
-template <typename RT>
+// (HeIII), T and the remaining time rem (0 after the last sub-step).  COUNT
+// (diffuse recombination field): adds to nrec[] the recombinations straight
+// to the ground state of H I, He I, He II per cm^3 in the sub-step,
+// (alpha_A - alpha_B) n_e n_ion (at least 0) with the rates at the
+// sub-step's starting temperature and n_e and the ions at its end, as in
+// the backward-Euler update.
+template <typename RT, bool COUNT>
 __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, double& y3, double& T,
-                                        double& rem, int nsub) {
+                                        double& rem, int nsub, double* nrec) {
   const bool coll = (c.mask & 2) != 0, rec = (c.mask & 4) != 0, diel = (c.mask & 32) != 0;
   const bool he = c.nHe > 0.0;
   const Rates r = rates_at<RT>(T, c.caseB);
+  double gH = 0.0, g2 = 0.0, g3 = 0.0;
+  if (COUNT && c.count_rec && rec) {
+    const Rates rB = rates_at<RT>(T, 1);
+    gH = fmax(r.aHII - rB.aHII, 0.0);
+    g2 = fmax(r.aHeII - rB.aHeII, 0.0);
+    g3 = fmax(r.aHeIII - rB.aHeIII, 0.0);
+  }
   const double aH = rec ? r.aHII : 0.0;
   const double aHe2 = rec ? r.aHeII + (diel ? r.adiel : 0.0) : 0.0;
   const double aHe3 = rec ? r.aHeIII : 0.0;
@@ -206,6 +218,13 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
     const double ntot2 = c.nH + c.nHe + ne2;
     T = (1.5 * kB * ntot * T + h * (heat + Cc * c.Tcmb)) / (1.5 * kB * ntot2 + h * (L1 + Cc));
   }
+  if (COUNT && c.count_rec && rec) {
+    nrec[0] += h * gH * ne2 * (c.nH * xn);
+    if (he) {
+      nrec[1] += h * g2 * ne2 * (c.nHe * y2n);
+      nrec[2] += h * g3 * ne2 * (c.nHe * y3n);
+    }
+  }
   x = xn;
   y2 = y2n;
   y3 = y3n;
@@ -240,7 +259,10 @@ __device__ __forceinline__ void load_cell(const StepArgs& a, int64_t i, int b, C
   const long long nabs = (dHI + dHeI) + dHeII;
   c.eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
   c.iso = M->isothermal;
-  c.caseB = M->caseB;
+  // the diffuse recombination field replaces on-the-spot absorption: case A
+  c.caseB = M->f_rec > 0.0 ? 0 : M->caseB;
+  c.count_rec = M->f_rec > 0.0;
+  c.V = V;
   c.Tcmb = M->T_cmb;
   c.mask = a.cool_mask;
   if (M->T_cmb > 0 && (a.cool_mask & 16)) {
@@ -258,7 +280,7 @@ __device__ __forceinline__ void load_cell(const StepArgs& a, int64_t i, int b, C
 // on a step counter) as soon as its cell is done.  Cells need from one to
 // thousands of sub-steps, so handing out work per lane keeps the warps full
 // instead of waiting for the slowest cell of a fixed group of 32.
-template <typename RT>
+template <typename RT, bool COUNT>
 __global__ void __launch_bounds__(128) k_chemistry(StepArgs a, unsigned long long* next_cell) {
   const unsigned full = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
@@ -269,6 +291,7 @@ __global__ void __launch_bounds__(128) k_chemistry(StepArgs a, unsigned long lon
   double x = 0, y2 = 0, y3 = 0, T = 0, rem = 0;
   int nsub = 0;
   unsigned long long subs = 0;
+  double nrec[3] = {0.0, 0.0, 0.0};
   bool need = true, exhausted = false;
   while (true) {
     const unsigned m = __ballot_sync(full, need && !exhausted);
@@ -292,6 +315,7 @@ __global__ void __launch_bounds__(128) k_chemistry(StepArgs a, unsigned long lon
           load_cell(a, i, b, c, x, y2, y3, T);
           rem = a.dt;
           nsub = 0;
+          if (COUNT) nrec[0] = nrec[1] = nrec[2] = 0.0;
           need = false;
         }
       }
@@ -299,13 +323,15 @@ __global__ void __launch_bounds__(128) k_chemistry(StepArgs a, unsigned long lon
     const bool active = !need;
     if (!__any_sync(full, active)) break;
     if (active) {
-      substep<RT>(c, x, y2, y3, T, rem, nsub);
+      substep<RT, COUNT>(c, x, y2, y3, T, rem, nsub, nrec);
       ++nsub;
       if (!(rem > 0.0)) {
         a.xHII[i] = x;
         a.xHeII[i] = y2;
         a.xHeIII[i] = y3;
         a.T[i] = T;
+        if (COUNT && c.count_rec)
+          for (int sp = 0; sp < 3; ++sp) a.rec[(int64_t)sp * n + i] += nrec[sp] * c.V;
         subs += (unsigned long long)nsub;
         need = true;
       }
@@ -321,6 +347,11 @@ void launch_chemistry(const StepArgs& a, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t blocks = std::min<int64_t>((a.n_cells_total + 127) / 128, (int64_t)sms * 8);
   cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
-  if (a.fp32_rates) k_chemistry<float><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
-  else k_chemistry<double><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
+  if (a.any_rec) {
+    if (a.fp32_rates) k_chemistry<float, true><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
+    else k_chemistry<double, true><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
+  } else {
+    if (a.fp32_rates) k_chemistry<float, false><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
+    else k_chemistry<double, false><<<(unsigned)blocks, 128, 0, s>>>(a, a.work);
+  }
 }

@@ -85,6 +85,31 @@ __device__ __forceinline__ bool iso_direction_f32(uint64_t seed, uint32_t step, 
   return false;
 }
 
+// Start of the re-emission packet of a cell (diffuse recombination field):
+// the offsets (in cells) of a point drawn uniformly in the cell.  The
+// packet uses the Philox counters of a source 0x80000000 | (cell >> 32) and
+// packet cell & 0xffffffff (cell: index within its box), so no point source
+// shares them; its direction takes attempts 0..63 as for a source packet,
+// the offsets attempts 64 (x, y) and 65 (z), each the top 31 bits of a
+// 64-bit word times 2^-31 (cell + offset is exact in FP64 and below the
+// next cell).
+__device__ __forceinline__ double uniform31(uint32_t lo, uint32_t hi) {
+  unsigned long long w = ((unsigned long long)hi << 32) | (unsigned long long)lo;
+  return (double)(w >> 33) * 4.656612873077392578125e-10;   // 2^-31
+}
+__device__ __forceinline__ uint32_t rec_src_id(int64_t cell) {
+  return 0x80000000u | (uint32_t)((unsigned long long)cell >> 32);
+}
+__device__ __forceinline__ void rec_offsets(uint64_t seed, uint32_t step, int64_t cell, double& ox,
+                                            double& oy, double& oz) {
+  const uint32_t src = rec_src_id(cell), pkt = (uint32_t)cell;
+  const uint4 r0 = philox10(make_uint4(pkt, src, step, 64u), seed);
+  const uint4 r1 = philox10(make_uint4(pkt, src, step, 65u), seed);
+  ox = uniform31(r0.x, r0.y);
+  oy = uniform31(r0.z, r0.w);
+  oz = uniform31(r1.x, r1.y);
+}
+
 // ---------------------------------------------------------------- exp(-tau)
 // e^-tau, tau >= 0: split -tau = k ln2 + r (Cody & Waite 1980 two-constant
 // reduction, ln2 high part with 40 significant bits), e^r by its degree-13

@@ -751,6 +751,68 @@ __global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables 
   }
 }
 
+// One re-emission packet per entry of this step's list (diffuse
+// recombination field), traced to the end by its own thread: start point
+// and direction from the cell's Philox counters, the photons of each species
+// in its bin held as 32-bit counts of 2^e quanta as for a source packet.
+// Entries are read in any order: deposits and counts do not depend on it.
+template <int NBT, bool HE, bool HEAT>
+__global__ void __launch_bounds__(256, 3) k_rec_mixed(StepArgs a, BinTables t) {
+  const int nb = NBT > 0 ? NBT : t.n_bins;
+  const int64_t n = (int64_t)*a.rec_count;
+  const uint32_t step = (uint32_t)*a.step_dev;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = base + threadIdx.x;
+    Tally tl{0, 0, 0, 0u, 0u};
+    int b = -1;
+    if (e < n) {
+      const long long* L = a.rec_list + 4 * e;
+      const int64_t g = L[0];
+      b = box_of_cell(a.boxes, a.n_boxes, g);
+      const BoxMeta* M = a.boxes + b;
+      const int64_t cell = g - M->cell_off;
+      float fx, fy, fz;
+      if (!iso_direction_f32(M->seed, step, rec_src_id(cell), (uint32_t)cell, fx, fy, fz)) {
+        atomicOr(a.err, ERR_DIRECTION);
+      } else {
+        unsigned long long q[NBT > 0 ? NBT : CRASH_MAX_BINS];
+        for (int j = 0; j < nb; ++j) q[j] = 0ull;
+        for (int s = 0; s < 3; ++s)
+          if (a.rec_bin[s] >= 0) q[a.rec_bin[s]] += (unsigned long long)L[1 + s];
+        unsigned long long qmax = 0;
+        for (int j = 0; j < nb; ++j) qmax = q[j] > qmax ? q[j] : qmax;
+        Content<NBT> N;
+        const int bits = qmax ? 64 - __clzll((long long)qmax) : 0;
+        N.e = bits > 32 ? bits - 32 : 0;
+        for (int j = 0; j < nb; ++j) N.m[j] = (unsigned)(q[j] >> N.e);
+        tl.emitted += N.total(nb);
+        tl.packets += 1;
+        double ox, oy, oz;
+        rec_offsets(M->seed, step, cell, ox, oy, oz);
+        int ix = (int)(cell % M->nx), iy = (int)((cell / M->nx) % M->ny);
+        int iz = (int)(cell / ((int64_t)M->nx * M->ny));
+        const float px = (float)((double)ix + ox), py = (float)((double)iy + oy);
+        const float pz = (float)((double)iz + oz);
+        float tMx = fx > 0.f ? ((float)(ix + 1) - px) / fx : (fx < 0.f ? ((float)ix - px) / fx : INFINITY);
+        float tMy = fy > 0.f ? ((float)(iy + 1) - py) / fy : (fy < 0.f ? ((float)iy - py) / fy : INFINITY);
+        float tMz = fz > 0.f ? ((float)(iz + 1) - pz) / fz : (fz < 0.f ? ((float)iz - pz) / fz : INFINITY);
+        const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
+                                                 nb, M->max_iter, tl);
+        if (r == ESCAPED) tl.escaped += N.total(nb);
+        else if (r == ALIVE) atomicOr(a.err, ERR_DDA_LIMIT);
+      }
+    }
+    flush_warp(a, b, tl);
+  }
+}
+
+int num_sms();
+
+template <int NBT, bool HE, bool HEAT>
+void launch_rec_t(const StepArgs& a, const BinTables& t, cudaStream_t s) {
+  k_rec_mixed<NBT, HE, HEAT><<<(unsigned)(num_sms() * 3), 256, 0, s>>>(a, t);
+}
+
 // ------------------------------------------------------------------ passes
 template <int NBT, bool HE, bool HEAT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_pass_mixed(StepArgs a, BinTables t, WFArgs w, int S) {
@@ -1237,3 +1299,18 @@ void wavefront_destroy(void* p) {
 }
 
 int64_t wavefront_capacity(void* p) { return p ? ((WF*)p)->cap : 0; }
+
+int launch_rec_mixed(const StepArgs& a, const BinTables& t, cudaStream_t s) {
+  const bool he = a.any_he != 0, heat = a.any_heat != 0;
+  if (t.n_bins == 1) {
+    if (he) { if (heat) launch_rec_t<1, true, true>(a, t, s); else launch_rec_t<1, true, false>(a, t, s); }
+    else { if (heat) launch_rec_t<1, false, true>(a, t, s); else launch_rec_t<1, false, false>(a, t, s); }
+  } else if (t.n_bins == 8) {
+    if (he) { if (heat) launch_rec_t<8, true, true>(a, t, s); else launch_rec_t<8, true, false>(a, t, s); }
+    else { if (heat) launch_rec_t<8, false, true>(a, t, s); else launch_rec_t<8, false, false>(a, t, s); }
+  } else {
+    if (he) { if (heat) launch_rec_t<0, true, true>(a, t, s); else launch_rec_t<0, true, false>(a, t, s); }
+    else { if (heat) launch_rec_t<0, false, true>(a, t, s); else launch_rec_t<0, false, false>(a, t, s); }
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}

@@ -75,6 +75,8 @@ extern "C" crash_status crash_transport_noalloc(const crash_grid_desc* grid, int
   const crash_grid_desc& d = *grid;
   if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.box_cm > 0))
     return fail(CRASH_ERR_ARG, "grid dimensions and box_cm must be positive");
+  if (d.f_rec != 0.0)
+    return fail(CRASH_ERR_ARG, "the allocation-free call traces source packets only: f_rec must be 0");
   if (d.nx > 65535 || d.ny > 65535 || d.nz > 65535 || (int64_t)d.nx * d.ny * d.nz >= ((int64_t)1 << 31))
     return fail(CRASH_ERR_OVERFLOW, "each axis <= 65535 cells and < 2^31 cells");
   if (n_src < 1 || n_src > kMaxSources)

@@ -25,6 +25,7 @@ CRASH_FP64_PLAIN, CRASH_MIXED = 0, 1
 F_XHII, F_XHEII, F_XHEIII, F_T = 0, 1, 2, 3
 F_DEP_HI, F_DEP_HEI, F_DEP_HEII, F_DEP_E = 4, 5, 6, 7
 F_BUDGET, F_NH, F_TOTALS = 8, 9, 10
+F_REC_HI, F_REC_HEI, F_REC_HEII = 11, 12, 13
 
 EXPORTED = [
     "crash_default_opts", "crash_init_grid", "crash_init_batch", "crash_add_sources",
@@ -44,7 +45,8 @@ class crash_grid_desc(C.Structure):
                 ("x_HeIII", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double)),
                 ("x_HII0", C.c_double), ("x_HeII0", C.c_double), ("x_HeIII0", C.c_double),
                 ("T0", C.c_double), ("isothermal", C.c_int), ("caseB", C.c_int),
-                ("z_compton", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int)]
+                ("z_compton", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int),
+                ("f_rec", C.c_double)]
 
 
 class crash_run_opts(C.Structure):
@@ -143,6 +145,7 @@ def make_desc(box, precision=CRASH_FP64_PLAIN, keep=None):
     d.x_HII0, d.x_HeII0, d.x_HeIII0, d.T0 = box.x_HII0, box.x_HeII0, box.x_HeIII0, box.T0
     d.isothermal, d.caseB, d.z_compton, d.seed = box.isothermal, box.caseB, box.z_compton, box.seed
     d.precision = precision
+    d.f_rec = getattr(box, "f_rec", 0.0)
     return d
 
 

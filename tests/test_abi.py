@@ -34,13 +34,13 @@ def test_struct_layouts_match_header(tmp_path):
     probe = tmp_path / "probe.c"
     probe.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crash.h"\n'
                      'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(crash_grid_desc),'
-                     ' sizeof(crash_run_opts), offsetof(crash_grid_desc, precision),'
+                     ' sizeof(crash_run_opts), offsetof(crash_grid_desc, f_rec),'
                      ' offsetof(crash_run_opts, pass_limit));return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HDR), str(probe), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [C.sizeof(native.crash_grid_desc), C.sizeof(native.crash_run_opts),
-                   native.crash_grid_desc.precision.offset, native.crash_run_opts.pass_limit.offset]
+                   native.crash_grid_desc.f_rec.offset, native.crash_run_opts.pass_limit.offset]
 
 
 def test_argument_errors_are_status_codes():
@@ -57,6 +57,10 @@ def test_argument_errors_are_status_codes():
     d.nx = 4
     d.box_cm = -1.0
     assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
+    d.box_cm = 1.0
+    d.f_rec = 1.5                     # the re-emission threshold is a fraction
+    assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
+    d.f_rec = 0.0
     assert L.crash_step(None, 1.0, 1) == native.CRASH_ERR_ARG
     assert L.crash_free(None) == native.CRASH_ERR_ARG
     o = native.default_opts()
