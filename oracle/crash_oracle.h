@@ -8,8 +8,9 @@
  * (the CUDA library) never calls it and shares no code with it.
  *
  * Paper sections followed: Sec. 2 (packet emission, Eq. 1 attenuation,
- * species split, ionisation network, continuous processes, termination) and
- * Sec. 3.2 (N_p/N_t packets per source per step, sub-sampled chemistry).
+ * species split, ionisation network, continuous processes, termination,
+ * diffuse recombination field), Sec. 3 (re-emission of the diffuse field)
+ * and Sec. 3.2 (N_p/N_t packets per source per step, sub-sampled chemistry).
  */
 #ifndef CRASH_ORACLE_H
 #define CRASH_ORACLE_H
