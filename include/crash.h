@@ -121,6 +121,9 @@ typedef struct {
                                 (0 = as many as the grid needs).  A packet still alive after
                                 the last pass is a device-side limit: the next synchronising
                                 call returns CRASH_ERR_TIMEOUT. */
+  int sort_curve;            /* mixed form: order of the buckets in the re-sort key,
+                                0 = Morton (Z) curve, 1 = Hilbert curve.  Results do not
+                                depend on it (only the order packets are traced in). */
 } crash_run_opts;
 
 void crash_default_opts(crash_run_opts* o);

@@ -110,6 +110,60 @@ __device__ __forceinline__ void rec_offsets(uint64_t seed, uint32_t step, int64_
   oz = uniform31(r1.x, r1.y);
 }
 
+// ------------------------------------------------------ space-filling keys
+// Key of bucket (x, y, z), each coordinate below 2^b, along a space-filling
+// curve of 2^(3b) positions: the Morton (Z) order interleaves the bits, x
+// least significant; the Hilbert order first maps the coordinates to the
+// curve's transposed index by Skilling's transform (AIP Conf. Proc. 707,
+// 2004: undo the excess rotations and reflections level by level, then
+// Gray-encode) and interleaves that, x most significant.  Consecutive
+// Hilbert keys are face neighbours; consecutive Morton keys may jump.
+__host__ __device__ __forceinline__ unsigned spread_bits3(unsigned v) {   // 10 bits -> every third bit
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__host__ __device__ __forceinline__ unsigned curve_key3(unsigned x, unsigned y, unsigned z, int b,
+                                                        bool hilbert) {
+  if (!hilbert) return spread_bits3(x) | (spread_bits3(y) << 1) | (spread_bits3(z) << 2);
+  if (b <= 0) return 0u;
+  unsigned X0 = x, X1 = y, X2 = z;
+  const unsigned M = 1u << (b - 1);
+  for (unsigned Q = M; Q > 1u; Q >>= 1) {
+    const unsigned P = Q - 1u;
+    // axis 0: invert the low bits when its Q bit is set
+    if (X0 & Q) X0 ^= P;
+    // axes 1, 2: invert axis 0's low bits, or exchange them with axis i's
+    if (X1 & Q) {
+      X0 ^= P;
+    } else {
+      const unsigned t = (X0 ^ X1) & P;
+      X0 ^= t;
+      X1 ^= t;
+    }
+    if (X2 & Q) {
+      X0 ^= P;
+    } else {
+      const unsigned t = (X0 ^ X2) & P;
+      X0 ^= t;
+      X2 ^= t;
+    }
+  }
+  X1 ^= X0;
+  X2 ^= X1;
+  unsigned t = 0;
+  for (unsigned Q = M; Q > 1u; Q >>= 1)
+    if (X2 & Q) t ^= Q - 1u;
+  X0 ^= t;
+  X1 ^= t;
+  X2 ^= t;
+  return (spread_bits3(X0) << 2) | (spread_bits3(X1) << 1) | spread_bits3(X2);
+}
+
 // ---------------------------------------------------------------- exp(-tau)
 // e^-tau, tau >= 0: split -tau = k ln2 + r (Cody & Waite 1980 two-constant
 // reduction, ln2 high part with 40 significant bits), e^r by its degree-13

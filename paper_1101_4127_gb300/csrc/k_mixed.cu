@@ -59,6 +59,7 @@ struct WFArgs {
   unsigned* bcount;
   int rs;
   int tile;                  // keys of 16^3-cell tiles (tile passes) instead of 8^3 buckets
+  int curve;                 // 0: Morton order of the buckets, 1: Hilbert order
   int64_t cap;
 };
 
@@ -583,25 +584,17 @@ __device__ __forceinline__ long long append_slot(bool alive, unsigned* count_out
   return (long long)base + __popc(m & ((1u << lane) - 1u));
 }
 
-__device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every third bit
-  v &= 0x3FFu;
-  v = (v | (v << 16)) & 0x030000FFu;
-  v = (v | (v << 8)) & 0x0300F00Fu;
-  v = (v | (v << 4)) & 0x030C30C3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
-// sort key: Morton order of the packet's 8^3-cell bucket (16^3-cell tile for
-// tile passes), then direction octant
+// sort key: the packet's 8^3-cell bucket (16^3-cell tile for tile passes)
+// along the Morton or Hilbert curve, then its direction octant
 __device__ __forceinline__ unsigned sort_key(const BoxMeta* boxes, int box, int ix, int iy, int iz,
-                                             float dx, float dy, float dz, int tile) {
+                                             float dx, float dy, float dz, int tile, int curve) {
   const unsigned oct = (dx < 0.f ? 1u : 0u) | (dy < 0.f ? 2u : 0u) | (dz < 0.f ? 4u : 0u);
   const int sh = tile ? 4 : 3;
-  const unsigned mort = spread3((unsigned)ix >> sh) | (spread3((unsigned)iy >> sh) << 1) |
-                        (spread3((unsigned)iz >> sh) << 2);
-  const unsigned base = tile ? (unsigned)boxes[box].tile_off : (unsigned)boxes[box].bucket_off;
-  return base + ((mort << 3) | oct);
+  const BoxMeta& M = boxes[box];
+  const unsigned pos = curve_key3((unsigned)ix >> sh, (unsigned)iy >> sh, (unsigned)iz >> sh,
+                                  tile ? M.tile_bits : M.bucket_bits, curve != 0);
+  const unsigned base = tile ? (unsigned)M.tile_off : (unsigned)M.bucket_off;
+  return base + ((pos << 3) | oct);
 }
 
 // Packet records, RS bytes each (RS = 32 + 4 n_bins rounded up to 16 bytes,
@@ -673,7 +666,7 @@ __device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& 
   }
   if (ok) store_record<NBT>(w.rec_out, w.rs, slot, ix, iy, iz, box, tMx, tMy, tMz, dx, dy, dz, N, nb);
   if (w.key) {
-    const unsigned k = ok ? sort_key(a.boxes, box, ix, iy, iz, dx, dy, dz, w.tile) : 0xFFFFFFFFu;
+    const unsigned k = ok ? sort_key(a.boxes, box, ix, iy, iz, dx, dy, dz, w.tile, w.curve) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
     if (ok) {
       const int lane = threadIdx.x & 31;
@@ -1057,9 +1050,10 @@ __global__ void k_check_drained(const unsigned* count, int* err) {
   if (*count != 0u) atomicOr(err, ERR_WATCHDOG);
 }
 
-WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys, int tile = 0) {
+WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys, int tile = 0, int curve = 0) {
   WFArgs w;
   w.tile = tile;
+  w.curve = curve;
   const int out = 1 - in;
   w.rec_in = wf->rec[in];
   w.rec_out = wf->rec[out];
@@ -1139,7 +1133,7 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
       cudaMemsetAsync(wf->count, 0, 4 * sizeof(unsigned), s);
       cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * nk, s);
       {
-        WFArgs w = wf_args(wf, cur, false, true, 1);
+        WFArgs w = wf_args(wf, cur, false, true, 1, o.sort_curve);
         int64_t blocks = (n + block - 1) / block;
         if (blocks > persistent * 4) blocks = persistent * 4;
         tic();
@@ -1158,7 +1152,7 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
         k_tile_list<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nk / 8 + 255) / 256, 4096)), 256, 0, s>>>(
             wf->boff, wf->count + cur, nk, wf->items, wf->count + 2);
         cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * nk, s);
-        WFArgs w = wf_args(wf, cur, true, true, 1);
+        WFArgs w = wf_args(wf, cur, true, true, 1, o.sort_curve);
         cudaMemsetAsync(w.count_out, 0, sizeof(unsigned), s);
         tic();
         k_tile_pass<NBT, HE, HEAT><<<num_sms(), kTileBlock, kTileSmem, s>>>(
@@ -1188,7 +1182,7 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
     for (int p = 0; p < passes; ++p) {
       const bool next_sorted = sorted_pass(p + 1);
       if (next_sorted) cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * wf->n_keys, s);
-      WFArgs w = wf_args(wf, cur, sorted_pass(p), next_sorted);
+      WFArgs w = wf_args(wf, cur, sorted_pass(p), next_sorted, 0, o.sort_curve);
       cudaMemsetAsync(w.count_out, 0, sizeof(unsigned), s);
       tic();
       if (p == 0) {

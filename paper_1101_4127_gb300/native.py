@@ -54,7 +54,8 @@ class crash_run_opts(C.Structure):
                 ("chem_eps", C.c_double), ("chem_max_sub", C.c_int), ("cool_mask", C.c_int),
                 ("block_size", C.c_int), ("seg_per_iter", C.c_int), ("resort_interval", C.c_int),
                 ("wavefront", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
-                ("reg_cap", C.c_int), ("tile", C.c_int), ("pass_limit", C.c_int)]
+                ("reg_cap", C.c_int), ("tile", C.c_int), ("pass_limit", C.c_int),
+                ("sort_curve", C.c_int)]
 
 
 def library_path() -> str:

@@ -35,12 +35,12 @@ def test_struct_layouts_match_header(tmp_path):
     probe.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crash.h"\n'
                      'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(crash_grid_desc),'
                      ' sizeof(crash_run_opts), offsetof(crash_grid_desc, f_rec),'
-                     ' offsetof(crash_run_opts, pass_limit));return 0;}\n')
+                     ' offsetof(crash_run_opts, sort_curve));return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HDR), str(probe), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [C.sizeof(native.crash_grid_desc), C.sizeof(native.crash_run_opts),
-                   native.crash_grid_desc.f_rec.offset, native.crash_run_opts.pass_limit.offset]
+                   native.crash_grid_desc.f_rec.offset, native.crash_run_opts.sort_curve.offset]
 
 
 def test_argument_errors_are_status_codes():

@@ -44,6 +44,10 @@ def test_mixed_budget_closes_and_launch_shapes_agree_bit_for_bit():
     got = _fields(_run(box, P, 2, dt, wavefront=1, tile=1))      # shared-memory tile passes
     for a, b in zip(ref, got):
         assert np.array_equal(a, b), "tile"
+    for curve_opts in [dict(sort_curve=1), dict(sort_curve=1, tile=1)]:   # Hilbert-ordered keys
+        got = _fields(_run(box, P, 2, dt, wavefront=1, **curve_opts))
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b), curve_opts
 
 
 def test_tile_passes_dense_tiles_bit_for_bit():
