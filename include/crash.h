@@ -122,7 +122,8 @@ typedef struct {
                                 the last pass is a device-side limit: the next synchronising
                                 call returns CRASH_ERR_TIMEOUT. */
   int sort_curve;            /* mixed form: order of the buckets in the re-sort key,
-                                0 = Morton (Z) curve, 1 = Hilbert curve.  Results do not
+                                0 = Morton (Z) curve, 1 = Hilbert curve; tile passes
+                                (tile = 1) always key by Morton tiles.  Results do not
                                 depend on it (only the order packets are traced in). */
 } crash_run_opts;
 

@@ -627,7 +627,12 @@ static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, i
     *nk += 2;
   }
   if (c->precision == CRASH_MIXED) {
-    int rc = launch_trace_mixed(a, c->tables, c->opts, c->wf, c->max_iter, c->stream,
+    // tile passes key packets by the Morton index of their 16^3 tile, which
+    // the tile kernel decodes back into the tile's position: the Hilbert
+    // option applies to the bucket keys of the other passes only
+    crash_run_opts o = c->opts;
+    if (o.tile) o.sort_curve = 0;
+    int rc = launch_trace_mixed(a, c->tables, o, c->wf, c->max_iter, c->stream,
                                 timing ? &c->events : nullptr, &c->ev_used);
     if (rc < 0) return set_err(c, CRASH_ERR_CUDA, "mixed transport launch failed");
     *nk += rc;
