@@ -1,6 +1,7 @@
 """Pins of the CPU oracle against what the paper and the mathematics fix:
 closed forms, invariants, textbook values and an independent Philox
 implementation.  CPU only."""
+import dataclasses
 import json
 import math
 import os
@@ -616,3 +617,25 @@ def test_reemission_far_from_equilibrium_keeps_the_budget_exact():
         g.step(5.0 * inputs.MYR_S, 20000)
         b = g.read(oracle.F_BUDGET)
         assert b[0] > 0 and b[1] >= 0 and b[2] >= 0 and b[0] == b[1] + b[2]
+
+
+def test_diffuse_field_restores_most_of_the_on_the_spot_stromgren_volume():
+    """Stroemgren sphere of the Test-1 set-up near equilibrium (24^3, 60 steps
+    of 25 Myr, about 12 recombination times).  The ionised volume scales as
+    1/alpha: case B over case A is alpha_A / alpha_B.  Re-emitting the
+    ground-state recombinations (case A + diffuse field) puts back most of
+    the photons that the on-the-spot approximation (case B) keeps local; the
+    rest leave through the three faces that meet at the corner source."""
+    def volume(f_rec, caseB):
+        w = inputs.stromgren_rec(n=24, packets=100_000)
+        box = dataclasses.replace(w.boxes[0], f_rec=f_rec, caseB=caseB)
+        g = oracle.OracleGrid.from_box(box)
+        for _ in range(60):
+            g.step(25.0 * inputs.MYR_S, 100_000)
+        return float(g.read(oracle.F_XHII).sum())
+
+    VB, VA, Vd = volume(0.0, 1), volume(0.0, 0), volume(0.1, 0)
+    rA, rB = oracle.rates(1e4, 0), oracle.rates(1e4, 1)
+    assert VB / VA == pytest.approx(rA[0] / rB[0], rel=0.05)
+    assert VA < Vd < VB
+    assert (Vd - VA) / (VB - VA) > 0.5
