@@ -115,8 +115,9 @@ typedef struct {
   int reg_cap;               /* mixed form: 1 = transport kernels capped at 64 registers
                                 (more resident warps), 0 = uncapped (tuned/default) */
   int tile;                  /* mixed form: 1 = tile passes (packets sorted into 16^3-cell
-                                tiles, absorbers of a tile staged in shared memory); 0 = passes
-                                of seg_per_iter cells over global memory */
+                                tiles; a tile's absorbers and deposits held in shared memory
+                                while its packets cross it); 0 = passes of seg_per_iter cells
+                                over global memory */
   int pass_limit;            /* mixed form: at most this many wavefront passes per chunk
                                 (0 = as many as the grid needs).  A packet still alive after
                                 the last pass is a device-side limit: the next synchronising
