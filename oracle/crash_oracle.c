@@ -230,10 +230,11 @@ or_ctx* oracle_init_grid(const or_grid_desc* d) {
   c->xHeIII = malloc(n * 8); c->T = malloc(n * 8);
   c->aHI = calloc(n, 8); c->aHeI = calloc(n, 8); c->aHeII = calloc(n, 8);
   c->dHI = calloc(n, 8); c->dHeI = calloc(n, 8); c->dHeII = calloc(n, 8); c->dE = calloc(n, 8);
-  for (int a = 0; a < 3; ++a) c->rec[a] = calloc(n, 8);
+  if (c->f_rec > 0)   /* counts of the diffuse field, only when it is on */
+    for (int a = 0; a < 3; ++a) c->rec[a] = calloc(n, 8);
   if (!c->nH || !c->xHII || !c->xHeII || !c->xHeIII || !c->T || !c->aHI || !c->aHeI ||
-      !c->aHeII || !c->dHI || !c->dHeI || !c->dHeII || !c->dE || !c->rec[0] || !c->rec[1] ||
-      !c->rec[2]) {
+      !c->aHeII || !c->dHI || !c->dHeI || !c->dHeII || !c->dE ||
+      (c->f_rec > 0 && (!c->rec[0] || !c->rec[1] || !c->rec[2]))) {
     oracle_free(c);
     return NULL;
   }
@@ -787,9 +788,10 @@ int oracle_read_fields(or_ctx* c, int f, void* out) {
     case OR_F_DEP_E: memcpy(out, c->dE, n * 8); return 0;
     case OR_F_BUDGET: memcpy(out, c->budget, sizeof c->budget); return 0;
     case OR_F_NH: memcpy(out, c->nH, n * 8); return 0;
-    case OR_F_REC_HI: memcpy(out, c->rec[0], n * 8); return 0;
-    case OR_F_REC_HEI: memcpy(out, c->rec[1], n * 8); return 0;
-    case OR_F_REC_HEII: memcpy(out, c->rec[2], n * 8); return 0;
+    case OR_F_REC_HI: case OR_F_REC_HEI: case OR_F_REC_HEII:
+      if (!c->rec[f - OR_F_REC_HI]) return fail(c, "the diffuse recombination field is off");
+      memcpy(out, c->rec[f - OR_F_REC_HI], n * 8);
+      return 0;
     default: return fail(c, "unknown field id");
   }
 }
@@ -802,9 +804,10 @@ int oracle_write_fields(or_ctx* c, int f, const void* in) {
     case OR_F_XHEII: memcpy(c->xHeII, in, n * 8); return 0;
     case OR_F_XHEIII: memcpy(c->xHeIII, in, n * 8); return 0;
     case OR_F_T: memcpy(c->T, in, n * 8); return 0;
-    case OR_F_REC_HI: memcpy(c->rec[0], in, n * 8); return 0;
-    case OR_F_REC_HEI: memcpy(c->rec[1], in, n * 8); return 0;
-    case OR_F_REC_HEII: memcpy(c->rec[2], in, n * 8); return 0;
+    case OR_F_REC_HI: case OR_F_REC_HEI: case OR_F_REC_HEII:
+      if (!c->rec[f - OR_F_REC_HI]) return fail(c, "the diffuse recombination field is off");
+      memcpy(c->rec[f - OR_F_REC_HI], in, n * 8);
+      return 0;
     default: return fail(c, "field is not writable");
   }
 }
