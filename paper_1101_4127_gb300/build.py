@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in res:
             sys.stderr.write(log)
     tmp = SO + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-shared", "-o", tmp] + [o for o, _ in res] + ARCH + ["-lcudart"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + [o for o, _ in res] + ARCH + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)

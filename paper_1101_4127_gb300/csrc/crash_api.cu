@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "crash_internal.cuh"
 
 namespace {
@@ -613,8 +615,17 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
   return a;
 }
 
+// NVTX range over a phase of the host-side launch sequence, so that a
+// profiler can select the kernels of one phase (ncu --nvtx --nvtx-include);
+// without a profiler attached a range costs a few nanoseconds
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 // the launch sequence of one step (everything on c->stream)
 static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, int64_t* nk) {
+  NvtxRange step_range("crash step");
   CK(cudaMemsetAsync(c->budget, 0, 64 * (size_t)c->n_boxes, c->stream));
   launch_prep(a, c->precision, c->stream);
   if (c->any_rec) launch_rec_max(a, c->stream);      // the quantum covers the re-emission
@@ -626,43 +637,49 @@ static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, i
     launch_rec_select(a, c->stream);
     *nk += 2;
   }
-  if (c->precision == CRASH_MIXED) {
-    // tile passes key packets by the Morton index of their 16^3 tile, which
-    // the tile kernel decodes back into the tile's position: the Hilbert
-    // option applies to the bucket keys of the other passes only
-    crash_run_opts o = c->opts;
-    if (o.tile) o.sort_curve = 0;
-    int rc = launch_trace_mixed(a, c->tables, o, c->wf, c->max_iter, c->stream,
-                                timing ? &c->events : nullptr, &c->ev_used);
-    if (rc < 0) return set_err(c, CRASH_ERR_CUDA, "mixed transport launch failed");
-    *nk += rc;
-  } else {
-    *nk += 1;
-    if (timing) {
-      if (c->ev_used >= (int)c->events.size()) {
-        cudaEvent_t e0, e1;
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        c->events.push_back({e0, e1});
-      }
-      CK(cudaEventRecord(c->events[c->ev_used].first, c->stream));
-    }
-    launch_trace_fp64(a, c->tables, c->opts.block_size, c->stream);
-    if (timing) {
-      CK(cudaEventRecord(c->events[c->ev_used].second, c->stream));
-      c->ev_used++;
-    }
-  }
-  if (c->any_rec) {
+  {
+    NvtxRange transport_range("transport");
     if (c->precision == CRASH_MIXED) {
-      if (launch_rec_mixed(a, c->tables, c->stream) < 0)
-        return set_err(c, CRASH_ERR_CUDA, "re-emission launch failed");
+      // tile passes key packets by the Morton index of their 16^3 tile, which
+      // the tile kernel decodes back into the tile's position: the Hilbert
+      // option applies to the bucket keys of the other passes only
+      crash_run_opts o = c->opts;
+      if (o.tile) o.sort_curve = 0;
+      int rc = launch_trace_mixed(a, c->tables, o, c->wf, c->max_iter, c->stream,
+                                  timing ? &c->events : nullptr, &c->ev_used);
+      if (rc < 0) return set_err(c, CRASH_ERR_CUDA, "mixed transport launch failed");
+      *nk += rc;
     } else {
-      launch_rec_fp64(a, c->tables, c->stream);
+      *nk += 1;
+      if (timing) {
+        if (c->ev_used >= (int)c->events.size()) {
+          cudaEvent_t e0, e1;
+          CK(cudaEventCreate(&e0));
+          CK(cudaEventCreate(&e1));
+          c->events.push_back({e0, e1});
+        }
+        CK(cudaEventRecord(c->events[c->ev_used].first, c->stream));
+      }
+      launch_trace_fp64(a, c->tables, c->opts.block_size, c->stream);
+      if (timing) {
+        CK(cudaEventRecord(c->events[c->ev_used].second, c->stream));
+        c->ev_used++;
+      }
     }
-    *nk += 1;
+    if (c->any_rec) {
+      if (c->precision == CRASH_MIXED) {
+        if (launch_rec_mixed(a, c->tables, c->stream) < 0)
+          return set_err(c, CRASH_ERR_CUDA, "re-emission launch failed");
+      } else {
+        launch_rec_fp64(a, c->tables, c->stream);
+      }
+      *nk += 1;
+    }
+  }   // transport range
+  if (c->opts.chemistry) {
+    NvtxRange chem_range("chemistry");
+    launch_chemistry(a, c->stream);
   }
-  if (c->opts.chemistry) launch_chemistry(a, c->stream);
   k_end_step<<<(8 * c->n_boxes + 255) / 256, 256, 0, c->stream>>>(c->step_dev, c->budget,
                                                                     c->totals, c->n_boxes);
   CK(cudaGetLastError());
