@@ -320,9 +320,10 @@ def run_crash(args):
             if hold:
                 g.checkpoint(native.CKPT_RESTORE_STATE)   # tune on the state that is timed
             g.sync()
-            tuned = g.autotune(w.dt_s, Plist)   # block, crossings per pass, re-sort, reg cap
+            # block, crossings per pass, re-sort, register cap, tiles, key curve
+            tuned = g.autotune(w.dt_s, Plist)
             tuned_kw.update(block_size=tuned[0], seg_per_iter=tuned[1], resort_interval=tuned[2],
-                            reg_cap=tuned[3], tile=tuned[4])
+                            reg_cap=tuned[3], tile=tuned[4], sort_curve=tuned[5])
             g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0, **tuned_kw)
     g.sync()
     g.reset_kernel_time()
@@ -473,7 +474,8 @@ def run_crash(args):
             "fp64_plain": fp64,
             "autotuned": {"block": tuned[0], "crossings_per_pass": tuned[1],
                           "resort_interval": tuned[2], "reg_cap": tuned[3],
-                          "tile": tuned[4]} if tuned else None,
+                          "tile": tuned[4], "sort_curve": ["morton", "hilbert"][tuned[5]]}
+                         if tuned else None,
             "gpu_launches": int(launches),
             "clocks": ck,
             "crossings_per_step": crossings / args.steps,

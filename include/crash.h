@@ -205,13 +205,14 @@ int64_t crash_launch_count(crash_ctx* ctx);
 
 /* Autotuner: times transport-only trial steps over block size, crossings
    per pass, re-sort interval, register cap and tile passes (mixed form) on
-   the current state, over a window of about one wavefront chunk of packet
-   ids; the state and the step index are restored afterwards.  Stores the
-   fastest in the context's options and returns the chosen values (outputs
-   may be NULL). */
+   the current state, over a window of about 2^26 packet ids, then the
+   fastest once more with Hilbert-ordered re-sort keys; the state, the
+   diffuse field's counts and the step index are restored afterwards.
+   Stores the fastest in the context's options and returns the chosen values
+   (outputs may be NULL). */
 crash_status crash_autotune(crash_ctx* ctx, double dt_s, const uint64_t* packets_per_box,
                             int* block_size, int* seg_per_iter, int* resort_interval,
-                            int* reg_cap, int* tile);
+                            int* reg_cap, int* tile, int* sort_curve);
 
 crash_status crash_free(crash_ctx* ctx);
 const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error */

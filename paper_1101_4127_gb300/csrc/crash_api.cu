@@ -899,7 +899,8 @@ extern "C" crash_status crash_reset_kernel_time(crash_ctx* c) {
 
 // ---------------------------------------------------------------- autotune
 extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* P, int* block,
-                                       int* seg, int* resort, int* reg_cap, int* tile) {
+                                       int* seg, int* resort, int* reg_cap, int* tile,
+                                       int* sort_curve) {
   if (!c || !P) return CRASH_ERR_ARG;
   cudaSetDevice(c->device);
   // save the state and the step index so that trials leave no trace
@@ -911,6 +912,12 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   CK(cudaMemcpy(save + n, c->xHeII, n * 8, cudaMemcpyDeviceToDevice));
   CK(cudaMemcpy(save + 2 * n, c->xHeIII, n * 8, cudaMemcpyDeviceToDevice));
   CK(cudaMemcpy(save + 3 * n, c->T, n * 8, cudaMemcpyDeviceToDevice));
+  // the diffuse field's counts too: trial steps re-emit and reset them
+  double* save_rec = nullptr;
+  if (c->any_rec) {
+    CK(cudaMalloc(&save_rec, n * 24));
+    CK(cudaMemcpy(save_rec, c->rec, n * 24, cudaMemcpyDeviceToDevice));
+  }
   unsigned long long step0 = 0;
   CK(cudaMemcpy(&step0, c->step_dev, 8, cudaMemcpyDeviceToHost));
   crash_run_opts base = c->opts;
@@ -945,8 +952,16 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
       for (int sg : segs)
         for (int rs : resorts) trials.push_back({bs, sg, rs, cap, 0});
   if (c->precision == CRASH_MIXED) trials.push_back({256, 0, 1, 0, 1});
-  for (const Trial& tr : trials) {
+  // the fastest configuration is then tried once more with Hilbert-ordered
+  // bucket keys (trial index -1)
+  for (int ti = 0; ti <= (int)trials.size(); ++ti) {
+    const bool curve_trial = ti == (int)trials.size();
+    if (curve_trial && (c->precision != CRASH_MIXED || best.tile || best_ms >= 1e300)) break;
+    const Trial tr = curve_trial ? Trial{best.block_size, best.seg_per_iter, best.resort_interval,
+                                         best.reg_cap, best.tile}
+                                 : trials[ti];
     crash_run_opts o = base;
+    o.sort_curve = curve_trial ? 1 : 0;
     o.block_size = tr.bs;
     o.seg_per_iter = tr.sg;
     o.resort_interval = tr.rs;
@@ -981,6 +996,7 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
       best.resort_interval = tr.rs;
       best.reg_cap = tr.cap;
       best.tile = tr.tile;
+      best.sort_curve = o.sort_curve;
     }
   }
   c->opts = best;
@@ -991,6 +1007,10 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   cudaMemcpy(c->T, save + 3 * n, n * 8, cudaMemcpyDeviceToDevice);
   cudaMemcpy(c->step_dev, &step0, 8, cudaMemcpyHostToDevice);
   cudaFree(save);
+  if (save_rec) {
+    cudaMemcpy(c->rec, save_rec, n * 24, cudaMemcpyDeviceToDevice);
+    cudaFree(save_rec);
+  }
   c->step_host = step0;
   if (st != CRASH_OK) return st;
   if (block) *block = best.block_size;
@@ -998,5 +1018,6 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
   if (resort) *resort = best.resort_interval;
   if (reg_cap) *reg_cap = best.reg_cap;
   if (tile) *tile = best.tile;
+  if (sort_curve) *sort_curve = best.sort_curve;
   return CRASH_OK;
 }

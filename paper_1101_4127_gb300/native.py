@@ -98,7 +98,7 @@ def lib(build_if_missing: bool = True):
             L.crash_launch_count.restype = C.c_int64
             L.crash_autotune.argtypes = [P, C.c_double, C.POINTER(C.c_uint64), C.POINTER(C.c_int),
                                          C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                         C.POINTER(C.c_int)]
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.crash_transport_noalloc.argtypes = [
                 C.POINTER(crash_grid_desc), C.c_int, dp, dp, C.c_int, dp, dp, C.c_double, C.c_uint64,
                 C.c_uint64, C.c_int, P, P, C.POINTER(C.c_int64), P]
@@ -239,11 +239,12 @@ class Grid:
         return self.L.crash_launch_count(self.ctx)
 
     def autotune(self, dt_s, packets):
+        """Returns (block_size, seg_per_iter, resort_interval, reg_cap, tile,
+        sort_curve) of the fastest trial, which the context keeps."""
         arr = (C.c_uint64 * len(packets))(*[int(p) for p in packets])
-        bs, sg, rs, rc, tl = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        self._check(self.L.crash_autotune(self.ctx, float(dt_s), arr, C.byref(bs), C.byref(sg),
-                                          C.byref(rs), C.byref(rc), C.byref(tl)))
-        return bs.value, sg.value, rs.value, rc.value, tl.value
+        out = [C.c_int() for _ in range(6)]
+        self._check(self.L.crash_autotune(self.ctx, float(dt_s), arr, *[C.byref(v) for v in out]))
+        return tuple(v.value for v in out)
 
     def close(self):
         if getattr(self, "ctx", None):
