@@ -1,6 +1,8 @@
 // crash_api.cu -- host runtime behind the C ABI of include/crash.h: context
 // and device memory, source tables, the per-step launch sequence (optionally
-// captured in a CUDA graph), field I/O, event timing and the autotuner.
+// captured in a CUDA graph; NVTX ranges mark its phases), the diffuse
+// recombination field's counts and re-emission, field I/O, checkpoints,
+// event timing and the autotuner.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>

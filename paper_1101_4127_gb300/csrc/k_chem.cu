@@ -24,6 +24,9 @@
 //   * fractions clamped to [0,1], He renormalised to unit sum;
 //   * 1.5 k (n_tot T)_new = 1.5 k (n_tot T)_old + h (H + C n_e T_cmb)
 //     - h (Lambda(T_old)/T_old + C n_e) T_new  (cooling linear in T_new).
+// With the diffuse recombination field on (f_rec > 0) the network uses case
+// A and counts the recombinations straight to the ground state of each ion,
+// which the next step re-emits as packets.
 #include <math.h>
 
 #include <algorithm>

@@ -11,6 +11,10 @@
 //   k_trace_fp64  one thread per packet: isotropic direction, content, and
 //              the cell-by-cell walk with Eq. 1 attenuation and int64
 //              deposition until the packet is empty or leaves the grid.
+//   k_rec_max, k_rec_select, k_rec_fp64  diffuse recombination field
+//              (Sec. 2): the largest count over threshold (for the step's
+//              quantum), this step's re-emitting cells, and one FP64 packet
+//              per such cell walked like a source packet.
 #include <math.h>
 
 #include <algorithm>
