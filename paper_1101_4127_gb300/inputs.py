@@ -205,6 +205,38 @@ def stromgren_rec(n: int = 128, packets: int = 1_000_000, steps: int = 20,
                     25.0 * MYR_S, "fp64")
 
 
+def blackbody_ionising_rate(L_erg_s: float, T_K: float) -> float:
+    """Photons per second above 13.6 eV of a black body of bolometric
+    luminosity L: L / (k T) times the photon integral of x^2 / (e^x - 1)
+    above x0 = 13.6 eV / kT (64-point Gauss-Legendre on [x0, x0 + 60]) over
+    the energy integral pi^4 / 15."""
+    kT_eV = 8.617333262e-5 * T_K
+    x0 = 13.6 / kT_eV
+    xg, wg = np.polynomial.legendre.leggauss(64)
+    a, b = x0, x0 + 60.0
+    x = 0.5 * (b - a) * xg + 0.5 * (b + a)
+    num = 0.5 * (b - a) * np.sum(wg * x * x / np.expm1(x))
+    return L_erg_s / (kT_eV * 1.602176634e-12) * num / (np.pi ** 4 / 15.0)
+
+
+def cloudy_hhe(n: int = 64, packets: int = 6_666_667, steps: int = 30) -> Workload:
+    """Test-3-like H II region in H+He (Sec. 4.2.3): uniform n = 1 cm^-3 of
+    90% H and 10% He by number, T from 100 K, a 6e4 K black body of 1e38
+    erg/s at the centre of a 128 pc box of n^3 cells, 8 bins; 6e5 yr in
+    `steps` steps, the paper's 2e8 packets spread over them.  Readings: the
+    source sits at the centre and x_HII0 = 1.2e-3 as in the other tests."""
+    E, f = blackbody_bins(6e4)
+    bE, bf = _bins_for(1, E, f)
+    box = Box(n=n, box_cm=128.0 * 3.0857e18, nH=None, nH0=0.9, he_over_h=0.1 / 0.9,
+              x_HII0=1.2e-3, x_HeII0=0.0, x_HeIII0=0.0, T0=100.0,
+              isothermal=0, caseB=1, z_compton=-1.0, seed=SEED_BASE + 9,
+              src_pos=np.array([[n / 2, n / 2, n / 2]]),
+              src_ndot=np.array([blackbody_ionising_rate(1e38, 6e4)]),
+              bin_eV=bE, bin_frac=bf)
+    return Workload(f"cloudy_hhe_{n}^3_1src_8bin", [box], [packets], steps,
+                    6e5 * 3.15576e7 / steps, "fp64")
+
+
 def hhe_blackbody_128(n: int = 128, packets: int = 10_000_000, steps: int = 50) -> Workload:
     """Test-2-like H+He expansion (Sec. 4.2.2) in a 6.6 kpc box of 128^3 cells,
     He/H = 0.08, T evolving from 100 K, corner 1e5 K black-body source of

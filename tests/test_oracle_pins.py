@@ -639,3 +639,39 @@ def test_diffuse_field_restores_most_of_the_on_the_spot_stromgren_volume():
     assert VB / VA == pytest.approx(rA[0] / rB[0], rel=0.05)
     assert VA < Vd < VB
     assert (Vd - VA) / (VB - VA) > 0.5
+
+
+def test_hhe_region_of_the_test3_setup_reaches_its_stromgren_radius():
+    """Test-3 set-up (6e4 K black body, 1e38 erg/s, n = 1 cm^-3 of 90% H and
+    10% He, T from 100 K) on 24^3 cells over 6e5 yr (about 4 recombination
+    times): the H II region's radius by volume comes within 15% of the
+    Stroemgren law r_S (1 - e^{-t/t_rec})^{1/3} at the region's own
+    temperature and electron density; photo-heating holds it between 1e4
+    and 3e4 K; a 6e4 K source leaves helium singly ionised; the spherically
+    averaged x_HII falls from ionised inside to neutral outside."""
+    from paper_1101_4127_gb300 import diagnostics as D
+    w = inputs.cloudy_hhe(n=24, packets=50_000)
+    box = w.boxes[0]
+    g = oracle.OracleGrid.from_box(box)
+    for _ in range(w.n_steps):
+        g.step(w.dt_s, 50_000)
+    x, T = g.read(oracle.F_XHII), g.read(oracle.F_T)
+    y2, y3 = g.read(oracle.F_XHEII), g.read(oracle.F_XHEIII)
+    ion = x > 0.5
+    Tm = float(T[ion].mean())
+    aB = oracle.rates(Tm, 1)[0]
+    nH, nHe = 0.9, 0.1
+    ne = nH + nHe * float((y2[ion] + 2 * y3[ion]).mean())
+    Q = float(box.src_ndot[0])
+    t = w.n_steps * w.dt_s
+    rS = (3 * Q / (4 * math.pi * aB * ne * nH)) ** (1 / 3)
+    r_t = rS * (1 - math.exp(-t * aB * ne)) ** (1 / 3)
+    dl = box.box_cm / box.n
+    r = D.front_radius(x) * dl
+    assert r == pytest.approx(r_t, rel=0.15)
+    assert 1e4 < Tm < 3e4
+    assert float(y2[ion].mean()) > 0.9
+    c = (box.n / 2, box.n / 2, box.n / 2)
+    R = r / dl
+    prof, _ = D.radial_profile(x, c, np.array([0.0, 0.5 * R, 1.3 * R, 2.0 * R]))
+    assert prof[0] > 0.9 and prof[2] < 0.1
