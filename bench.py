@@ -61,6 +61,8 @@ def workload(name):
         return inputs.stromgren_rec(n=128, packets=10_000_000), native.CRASH_MIXED
     if name == "stromgren_rec_128_fp64":
         return inputs.stromgren_rec(n=128, packets=10_000_000), native.CRASH_FP64_PLAIN
+    if name == "cloudy_hhe_64":          # Test-3 H+He set-up
+        return inputs.cloudy_hhe(n=64), native.CRASH_MIXED
     if name == "lognormal_512_neutral":
         return inputs.lognormal_512(thin=False), native.CRASH_MIXED
     raise SystemExit(f"unknown workload {name}")
