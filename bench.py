@@ -379,13 +379,15 @@ def run_crash(args):
 
     # end-to-end through the C ABI with host buffers (pinned): every step
     # uploads its inputs (the sources, and for the held thin state the four
-    # state fields), steps, and reads back x_HII and the budget
+    # state fields), steps, and reads back the four state fields (x_HII,
+    # x_HeII, x_HeIII, T) of every box and the budget
     e2e = None
     if rank == 0 and not args.no_e2e:
         g.set_options(timing=0, **tuned_kw)
         ncell = box.n ** 3
-        pin = lambda dt_: torch.empty(ncell, dtype=dt_, pin_memory=True).numpy()
-        xh = pin(torch.float64)
+        pin = lambda dt_, n_=ncell: torch.empty(n_, dtype=dt_, pin_memory=True).numpy()
+        fields = (native.F_XHII, native.F_XHEII, native.F_XHEIII, native.F_T)
+        outs = [[pin(torch.float64, bx.n ** 3) for _ in fields] for bx in boxes]
         bud = np.empty(8, np.int64)
         state_in = []
         if hold:
@@ -396,11 +398,10 @@ def run_crash(args):
         nb = len(box.bin_eV)
         h2d = sum(bx.n_src for bx in boxes) * (3 + 1 + nb) * 8 + len(boxes) * nb * 8 + \
             sum(a_.nbytes for a_ in state_in)
-        d2h = xh.nbytes + bud.nbytes
+        d2h = sum(a_.nbytes for o_ in outs for a_ in o_) + len(boxes) * bud.nbytes
         t_e2e = 0.0
         cr_e2e = 0
-        n_e2e = max(1, min(args.steps, 3))
-        fields = (native.F_XHII, native.F_XHEII, native.F_XHEIII, native.F_T)
+        n_e2e = 5
         for _ in range(n_e2e):
             g.sync()
             t0 = time.perf_counter()
@@ -409,15 +410,17 @@ def run_crash(args):
             for i_, bx in enumerate(boxes):
                 g.add_sources(bx.src_pos, bx.src_ndot, bx.bin_eV, bx.bin_frac, box=i_)
             g.step(w.dt_s, step_arg)
-            g._check(g.L.crash_read_fields(g.ctx, native.F_XHII, xh.ctypes.data))
             cr_step = 0
             for i_ in range(len(boxes)):
+                for f_, a_ in zip(fields, outs[i_]):
+                    g._check(g.L.crash_read_fields_box(g.ctx, i_, f_, a_.ctypes.data))
                 g._check(g.L.crash_read_fields_box(g.ctx, i_, native.F_BUDGET, bud.ctypes.data))
                 cr_step += int(bud[3])
             t_e2e += time.perf_counter() - t0
             cr_e2e += cr_step
         e2e = {"value": cr_e2e / t_e2e, "unit": "crossings/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
+               "read_back": "x_HII, x_HeII, x_HeIII, T of every box, and the budget"}
 
     fp64 = None
     if rank == 0 and prec == native.CRASH_MIXED and not args.no_fp64 and not batch:

@@ -93,7 +93,9 @@ typedef struct {
                                 the cell re-emits it as one isotropic packet from a uniform
                                 point of the cell, in the lowest bin at or above the
                                 species' threshold; the count then restarts.  The photon
-                                quantum of the step gets two bits of headroom. */
+                                quantum of the step also keeps (cells of the box) x (largest
+                                count over its threshold) below 2^62 quanta, and then takes
+                                one more bit, so sources plus re-emission fit in int64. */
 } crash_grid_desc;
 
 /* Run options (crash_default_opts fills the defaults). */
@@ -236,21 +238,28 @@ const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error
        1 <= n_src <= CRASH_NOALLOC_MAX_SOURCES (larger counts are rejected
        with CRASH_ERR_OVERFLOW), 1 <= n_bins <= 16.
      dt_s, step_index, packets_per_step: as in crash_step (step_index is the
-       Philox step word); seg_per_pass: cells per wavefront pass (0 = 32).
-     absorbers_dev: device float[nx*ny*nz][4] = n_HI, n_HeI, n_HeII, 0 (cm^-3).
-     deposits_dev: device uint64[nx*ny*nz][4] (HI, HeI, HeII, heat); the
-       call ADDS its deposits, the caller zeroes the buffer for a fresh step.
+       Philox step word); packets_per_step <= CRASH_NOALLOC_MAX_PACKETS
+       (larger steps: CRASH_ERR_OVERFLOW); seg_per_pass: cells per wavefront
+       pass (0 = 32).
+     absorbers_dev: device float[nx*ny*nz][4] = n_HI, n_HeI, n_HeII, 0 (cm^-3),
+       16-byte aligned (CRASH_ERR_ARG otherwise).
+     deposits_dev: device uint64[nx*ny*nz][4] (HI, HeI, HeII, heat), 8-byte
+       aligned (CRASH_ERR_ARG otherwise); the call ADDS its deposits, the
+       caller zeroes the buffer for a fresh step.
      budget_out: host int64[8], laid out as CRASH_F_BUDGET, written.
      stream: a cudaStream_t (NULL: the default stream).
    The first call on a device looks up the scratch address with that device
-   current (cudaGetSymbolAddress); make that first call before any stream
-   capture.  The call synchronises `stream` before it returns.  Every call
+   current (cudaGetSymbolAddress) and keeps it for the life of the process;
+   make that first call before any stream capture.  A cudaDeviceReset in the
+   caller's process invalidates the kept address: the call is unsupported
+   after one.  The call synchronises `stream` before it returns.  Every call
    shares the one scratch array: calls that overlap on the GPU (from several
    host threads, or on several streams of one device) race and must not be
    issued.  Errors: CRASH_ERR_ARG / CRASH_ERR_OVERFLOW for rejected
    arguments (nothing is launched), CRASH_ERR_CUDA, CRASH_ERR_TIMEOUT for a
    device-side bound; crash_noalloc_last_error() gives the message. */
 #define CRASH_NOALLOC_MAX_SOURCES 1024
+#define CRASH_NOALLOC_MAX_PACKETS (1ull << 30)   /* 16384 queue chunks of 65536 packets */
 crash_status crash_transport_noalloc(const crash_grid_desc* grid, int n_src, const double* pos_cells,
                                      const double* ndot, int n_bins, const double* bin_eV,
                                      const double* bin_frac, double dt_s, uint64_t step_index,

@@ -72,6 +72,13 @@ extern "C" crash_status crash_transport_noalloc(const crash_grid_desc* grid, int
   if (!grid || !pos_cells || !ndot || !bin_eV || !bin_frac || !absorbers_dev || !deposits_dev ||
       !budget_out)
     return fail(CRASH_ERR_ARG, "NULL argument");
+  // the transport gathers absorbers as float4 and adds deposits with 64-bit
+  // reductions: a misaligned buffer (an offset view, say) would fault on the
+  // GPU, so it is refused here, before anything is launched
+  if (((uintptr_t)absorbers_dev & 15u) != 0)
+    return fail(CRASH_ERR_ARG, "absorbers_dev must be 16-byte aligned");
+  if (((uintptr_t)deposits_dev & 7u) != 0)
+    return fail(CRASH_ERR_ARG, "deposits_dev must be 8-byte aligned");
   const crash_grid_desc& d = *grid;
   if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.box_cm > 0))
     return fail(CRASH_ERR_ARG, "grid dimensions and box_cm must be positive");
@@ -86,8 +93,10 @@ extern "C" crash_status crash_transport_noalloc(const crash_grid_desc* grid, int
   if (!(dt_s > 0) || !isfinite(dt_s)) return fail(CRASH_ERR_ARG, "dt must be positive");
   if (packets_per_step == 0 || packets_per_step % (uint64_t)n_src)
     return fail(CRASH_ERR_ARG, "packets_per_step must be a positive multiple of n_src");
+  if (packets_per_step > (uint64_t)CRASH_NOALLOC_MAX_PACKETS)
+    return fail(CRASH_ERR_OVERFLOW, "packets_per_step above CRASH_NOALLOC_MAX_PACKETS (2^30): split the "
+                                    "step into calls over packet windows of a context instead");
   const uint64_t Ns = packets_per_step / (uint64_t)n_src;
-  if (Ns > 0xFFFFFFFFull) return fail(CRASH_ERR_OVERFLOW, "more than 2^32-1 packets per source");
   if (seg_per_pass < 0) return fail(CRASH_ERR_ARG, "seg_per_pass must be >= 0");
   double mx = 0.0;
   for (int s = 0; s < n_src; ++s) {
@@ -170,7 +179,10 @@ extern "C" crash_status crash_transport_noalloc(const crash_grid_desc* grid, int
   }
   // the budget of this call starts at zero; the queue counters are cleared
   // by the wavefront launcher for every chunk
-  cudaMemsetAsync(base + kOffBudget, 0, 64, s);
+  {
+    const cudaError_t e = cudaMemsetAsync(base + kOffBudget, 0, 64, s);
+    if (e != cudaSuccess) return fail(CRASH_ERR_CUDA, std::string("clearing the budget: ") + cudaGetErrorString(e));
+  }
 
   StepArgs a;
   memset(&a, 0, sizeof a);

@@ -71,18 +71,31 @@ def test_noalloc_transport_matches_crash_step_two_calls():
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
+    """Host-side checks, before anything reaches the GPU: more sources or
+    packets than the static scratch holds, and device buffers whose
+    alignment the kernels' vector loads and 64-bit reductions need (nothing
+    is launched, so the fake addresses are never dereferenced)."""
     L = native.lib()
     box = small_hhe_box((8, 8, 8), n_src=1, seed=302)
     desc = native.make_desc(box, native.CRASH_MIXED)
-    n = 1025                               # one more than CRASH_NOALLOC_MAX_SOURCES
-    pos = np.full((n, 3), 1.5)
-    ndot = np.ones(n)
-    E = np.array([20.0])
-    frac = np.ones(n)
     dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
     budget = np.zeros(8, np.int64)
-    st = L.crash_transport_noalloc(C.byref(desc), n, dp(pos), dp(ndot), 1, dp(E), dp(frac), 1e12, 0,
-                                   n, 0, C.c_void_p(1), C.c_void_p(1),
-                                   budget.ctypes.data_as(C.POINTER(C.c_int64)), None)
-    assert st == native.CRASH_ERR_OVERFLOW
+
+    def call(n, P, absorbers, deposits):
+        pos = np.full((n, 3), 1.5)
+        ndot = np.ones(n)
+        E = np.array([20.0])
+        frac = np.ones(n)
+        return L.crash_transport_noalloc(C.byref(desc), n, dp(pos), dp(ndot), 1, dp(E), dp(frac), 1e12,
+                                         0, P, 0, C.c_void_p(absorbers), C.c_void_p(deposits),
+                                         budget.ctypes.data_as(C.POINTER(C.c_int64)), None)
+
+    n = 1025                               # one more than CRASH_NOALLOC_MAX_SOURCES
+    assert call(n, n, 256, 256) == native.CRASH_ERR_OVERFLOW
     assert b"CRASH_NOALLOC_MAX_SOURCES" in L.crash_noalloc_last_error()
+    assert call(4, 4 * ((1 << 30) // 4 + 1), 256, 256) == native.CRASH_ERR_OVERFLOW
+    assert b"CRASH_NOALLOC_MAX_PACKETS" in L.crash_noalloc_last_error()
+    assert call(4, 64, 256 + 8, 256) == native.CRASH_ERR_ARG      # float4 loads need 16 B
+    assert b"absorbers_dev" in L.crash_noalloc_last_error()
+    assert call(4, 64, 256, 256 + 4) == native.CRASH_ERR_ARG      # 64-bit reductions need 8 B
+    assert b"deposits_dev" in L.crash_noalloc_last_error()
