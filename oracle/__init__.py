@@ -50,7 +50,8 @@ class GridDesc(C.Structure):
                 ("x_HeIII", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double)),
                 ("x_HII0", C.c_double), ("x_HeII0", C.c_double), ("x_HeIII0", C.c_double),
                 ("T0", C.c_double), ("isothermal", C.c_int), ("caseB", C.c_int),
-                ("z_compton", C.c_double), ("seed", C.c_uint64), ("f_rec", C.c_double)]
+                ("z_compton", C.c_double), ("seed", C.c_uint64), ("f_rec", C.c_double),
+                ("coupling", C.c_int), ("periodic", C.c_int)]
 
 
 class ChemCell(C.Structure):
@@ -58,6 +59,8 @@ class ChemCell(C.Structure):
                 ("xHII", C.c_double), ("xHeII", C.c_double), ("xHeIII", C.c_double),
                 ("T", C.c_double), ("G_HI", C.c_double), ("G_HeI", C.c_double),
                 ("G_HeII", C.c_double), ("heat_per_ion", C.c_double),
+                ("S_HI", C.c_double), ("S_HeI", C.c_double), ("S_HeII", C.c_double),
+                ("heat_rate", C.c_double),
                 ("isothermal", C.c_int), ("caseB", C.c_int), ("T_cmb", C.c_double),
                 ("eps", C.c_double), ("max_sub", C.c_int), ("cool_mask", C.c_int),
                 ("count_rec", C.c_int), ("rec", C.c_double * 3)]
@@ -78,6 +81,7 @@ def lib():
             L.oracle_read_fields.argtypes = [P, C.c_int, P]
             L.oracle_write_fields.argtypes = [P, C.c_int, P]
             L.oracle_set_step_index.argtypes = [P, C.c_uint64]
+            L.oracle_set_chem_sample.argtypes = [P, C.c_uint32, C.c_double]
             L.oracle_free.argtypes = [P]
             L.oracle_free.restype = None
             L.oracle_last_error.argtypes = [P]
@@ -151,7 +155,8 @@ def chem_cell(dt: float, **kw):
     He I, He II."""
     c = ChemCell()
     defaults = dict(nH=1e-3, nHe=0.0, xHII=0.0, xHeII=0.0, xHeIII=0.0, T=1e4, G_HI=0.0,
-                    G_HeI=0.0, G_HeII=0.0, heat_per_ion=0.0, isothermal=0, caseB=1,
+                    G_HeI=0.0, G_HeII=0.0, heat_per_ion=0.0, S_HI=0.0, S_HeI=0.0, S_HeII=0.0,
+                    heat_rate=0.0, isothermal=0, caseB=1,
                     T_cmb=0.0, eps=0.1, max_sub=10000, cool_mask=C_ALL, count_rec=0)
     defaults.update(kw)
     for k, v in defaults.items():
@@ -177,7 +182,8 @@ class OracleGrid:
     def __init__(self, nx, ny, nz, box_cm, n_H=None, n_H0=1e-3, he_over_h=0.0,
                  x_HII=None, x_HeII=None, x_HeIII=None, T=None,
                  x_HII0=0.0, x_HeII0=0.0, x_HeIII0=0.0, T0=1e4,
-                 isothermal=0, caseB=1, z_compton=-1.0, seed=0, f_rec=0.0):
+                 isothermal=0, caseB=1, z_compton=-1.0, seed=0, f_rec=0.0, coupling=0,
+                 periodic=0):
         self.L = lib()
         self.shape = (nz, ny, nx)
         self.ncell = nx * ny * nz
@@ -203,6 +209,7 @@ class OracleGrid:
         d.x_HII0, d.x_HeII0, d.x_HeIII0, d.T0 = x_HII0, x_HeII0, x_HeIII0, T0
         d.isothermal, d.caseB, d.z_compton, d.seed = isothermal, caseB, z_compton, seed
         d.f_rec = f_rec
+        d.coupling, d.periodic = coupling, periodic
         self.ctx = self.L.oracle_init_grid(C.byref(d))
         if not self.ctx:
             raise RuntimeError("oracle_init_grid failed")
@@ -214,7 +221,8 @@ class OracleGrid:
                 he_over_h=box.he_over_h, x_HII0=box.x_HII0, x_HeII0=box.x_HeII0,
                 x_HeIII0=box.x_HeIII0, T0=box.T0, isothermal=box.isothermal,
                 caseB=box.caseB, z_compton=box.z_compton, seed=box.seed,
-                f_rec=getattr(box, "f_rec", 0.0))
+                f_rec=getattr(box, "f_rec", 0.0), coupling=getattr(box, "coupling", 0),
+                periodic=getattr(box, "periodic", 0))
         g.add_sources(box.src_pos, box.src_ndot, box.bin_eV, box.bin_frac)
         return g
 
@@ -244,6 +252,10 @@ class OracleGrid:
 
     def set_step_index(self, k):
         self._check(self.L.oracle_set_step_index(self.ctx, int(k)))
+
+    def set_chem_sample(self, stride, dep_scale=1.0):
+        """Timing sample of the per-cell update (CPU baseline only)."""
+        self._check(self.L.oracle_set_chem_sample(self.ctx, int(stride), float(dep_scale)))
 
     def read(self, field):
         if field == F_BUDGET:

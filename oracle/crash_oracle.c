@@ -56,6 +56,11 @@ struct or_ctx {
   double T_cmb;
   uint64_t seed;
   double f_rec;                               /* > 0: diffuse recombination field */
+  int coupling;                               /* 1: photon-conserving chemistry coupling */
+  int periodic;                               /* 1: periodic box, light-travel stop */
+  double path_limit;                          /* periodic: c dt / dl of this step (cells) */
+  uint32_t chem_stride;                       /* timing sample of the per-cell update */
+  double dep_scale;
   double *rec[3];                             /* ground-state recombination photons */
   double *nH, *xHII, *xHeII, *xHeIII, *T;
   double *aHI, *aHeI, *aHeII;                 /* frozen absorber densities */
@@ -225,6 +230,11 @@ or_ctx* oracle_init_grid(const or_grid_desc* d) {
   c->T_cmb = d->z_compton >= 0 ? 2.725 * (1.0 + d->z_compton) : 0.0;
   c->seed = d->seed;
   c->f_rec = d->f_rec > 0 ? d->f_rec : 0.0;
+  c->coupling = d->coupling ? 1 : 0;
+  c->periodic = d->periodic ? 1 : 0;
+  c->path_limit = INFINITY;
+  c->chem_stride = 1;
+  c->dep_scale = 1.0;
   size_t n = (size_t)c->ncell;
   c->nH = malloc(n * 8); c->xHII = malloc(n * 8); c->xHeII = malloc(n * 8);
   c->xHeIII = malloc(n * 8); c->T = malloc(n * 8);
@@ -277,6 +287,14 @@ int oracle_set_options(or_ctx* c, int chemistry, uint32_t pkt_begin, uint32_t pk
 int oracle_set_step_index(or_ctx* c, uint64_t step) {
   if (!c) return -1;
   c->step = step;
+  return 0;
+}
+
+int oracle_set_chem_sample(or_ctx* c, uint32_t chem_stride, double dep_scale) {
+  if (!c) return -1;
+  if (chem_stride < 1 || !(dep_scale > 0)) return fail(c, "bad chemistry sample");
+  c->chem_stride = chem_stride;
+  c->dep_scale = dep_scale;
   return 0;
 }
 
@@ -335,7 +353,11 @@ int or_freeze_absorbers(or_ctx* c) {
 
 /* ------------------------------------------------------------ transport */
 /* Walk one packet cell by cell (Amanatides & Woo 1987 in grid units; ties
-   step x before y before z).  In each cell with path l > 0: per bin j,
+   step x before y before z).  In a periodic box (Sec. 2) a packet that
+   crosses a face re-enters through the opposite one, and its walk ends
+   after the path c dt (the step's path_limit, in cells): the last segment is
+   cut there and what the packet still holds is counted with the escaped
+   photons (it leaves the step).  In each cell with path l > 0: per bin j,
    tau_j = l * sum_s n_s sigma_s,j; N' = rint(N exp(-tau_j)) (Eq. 1 in
    integer quanta); the absorbed A = N - N' goes to He I and He II by
    rint(A kappa_s / kappa) and the rest to H I (Sec. 2 species split);
@@ -366,12 +388,16 @@ int64_t or_trace_packet(or_ctx* c, const double pos[3], const double dir[3],
       return 0;
     }
   double t = 0.0;
-  const int max_iter = c->nx + c->ny + c->nz + 3;
-  for (int it = 0; it < max_iter; ++it) {
+  /* a path of length L crosses at most (|d_x| + |d_y| + |d_z|) L + 3 < 2 L + 3 faces */
+  const double tlim = c->periodic ? c->path_limit : INFINITY;
+  const int64_t max_iter = c->periodic ? (int64_t)(2.0 * tlim) + 4 : (int64_t)c->nx + c->ny + c->nz + 3;
+  for (int64_t it = 0; it < max_iter; ++it) {
     int a = 0;
     if (tMax[1] < tMax[a]) a = 1;
     if (tMax[2] < tMax[a]) a = 2;
     double tn = tMax[a];
+    const int stop = tn >= tlim;
+    if (stop) tn = tlim;
     double seg = tn - t;
     if (seg > 0) {
       int64_t cell = (int64_t)idx[0] + (int64_t)c->nx * ((int64_t)idx[1] + (int64_t)c->ny * idx[2]);
@@ -412,10 +438,17 @@ int64_t or_trace_packet(or_ctx* c, const double pos[3], const double dir[3],
       }
       if (left == 0) return crossings;
     }
+    if (stop) {
+      for (int j = 0; j < nb; ++j) *escaped += N[j];
+      return crossings;
+    }
     t = tn;
     tMax[a] += tDelta[a];
     idx[a] += step[a];
-    if (idx[a] < 0 || idx[a] >= n[a]) {
+    if (c->periodic) {
+      if (idx[a] < 0) idx[a] = n[a] - 1;
+      else if (idx[a] >= n[a]) idx[a] = 0;
+    } else if (idx[a] < 0 || idx[a] >= n[a]) {
       for (int j = 0; j < nb; ++j) *escaped += N[j];
       return crossings;
     }
@@ -524,9 +557,14 @@ int or_chem_cell(or_chem_t* c, double dt) {
     /* derivatives at the start of the sub-step */
     double IH = c->G_HI + bH * ne, RH = aH * ne;
     double I1 = c->G_HeI + bHe1 * ne, R2 = aHe2 * ne, I2 = c->G_HeII + bHe2 * ne, R3 = aHe3 * ne;
-    double dx = IH * (1.0 - x) - RH * x;
-    double dy1 = -I1 * y1 + R2 * y2;
-    double dy3 = I2 * y2 - R3 * y3;
+    /* constant-count photo-ionisation sources (photon-conserving coupling),
+       each on while its species is present at the start of the sub-step */
+    double sH = (1.0 - x) > 0.0 ? c->S_HI : 0.0;
+    double s1 = y1 > 0.0 ? c->S_HeI : 0.0;
+    double s2 = y2 > 0.0 ? c->S_HeII : 0.0;
+    double dx = (sH + IH * (1.0 - x)) - RH * x;
+    double dy1 = (-I1 * y1 + R2 * y2) - s1;
+    double dy3 = (s2 + I2 * y2) - R3 * y3;
     double dy2 = -dy1 - dy3;
     double h = rem;
     double v[5] = {1.0 - x, x, y1, y2, y3};
@@ -540,7 +578,8 @@ int or_chem_cell(or_chem_t* c, double dt) {
     double ntot = nH + nHe + ne;
     if (!c->isothermal) {
       double nHI = nH * (1.0 - x), nHII = nH * x;
-      double heat = c->heat_per_ion * (c->G_HI * nHI + c->G_HeI * nHe * y1 + c->G_HeII * nHe * y2);
+      double heat = c->heat_per_ion * (c->G_HI * nHI + c->G_HeI * nHe * y1 + c->G_HeII * nHe * y2) +
+                    c->heat_rate;
       double L = cooling(r, mask, ne, nHI, nHII, nHe * y1, nHe * y2, nHe * y3) +
                  ccomp * ne * (T - c->T_cmb);
       double dne = nH * dx + nHe * (dy2 + 2.0 * dy3);
@@ -553,18 +592,20 @@ int or_chem_cell(or_chem_t* c, double dt) {
     double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
     for (int it = 0; it < 4; ++it) {
       double IHn = c->G_HI + bH * nen, RHn = aH * nen;
-      xn = (x + h * IHn) / (1.0 + h * (IHn + RHn));
+      xn = (x + h * (sH + IHn)) / (1.0 + h * (IHn + RHn));
       if (nHe > 0) {
         double i1 = c->G_HeI + bHe1 * nen, r2 = aHe2 * nen;
         double i2 = c->G_HeII + bHe2 * nen, r3 = aHe3 * nen;
         double a11 = 1.0 + h * i1, a12 = -h * r2;
         double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
         double a32 = -h * i2, a33 = 1.0 + h * r3;
-        double c1 = a12 / a11, d1 = y1 / a11;
+        /* right-hand side: the old fractions plus the constant sources */
+        double b1 = y1 - h * s1, b2 = y2 + h * (s1 - s2), b3 = y3 + h * s2;
+        double c1 = a12 / a11, d1 = b1 / a11;
         double m2 = a22 - a21 * c1;
-        double c2 = a23 / m2, d2 = (y2 - a21 * d1) / m2;
+        double c2 = a23 / m2, d2 = (b2 - a21 * d1) / m2;
         double m3 = a33 - a32 * c2;
-        y3n = (y3 - a32 * d2) / m3;
+        y3n = (b3 - a32 * d2) / m3;
         y2n = d2 - c2 * y3n;
         y1n = d1 - c1 * y2n;
       }
@@ -587,7 +628,8 @@ int or_chem_cell(or_chem_t* c, double dt) {
     double nen2 = nH * xn + nHe * (y2n + 2.0 * y3n);
     if (!c->isothermal) {
       double nHI = nH * (1.0 - xn), nHII = nH * xn;
-      double heat = c->heat_per_ion * (c->G_HI * nHI + c->G_HeI * nHe * y1n + c->G_HeII * nHe * y2n);
+      double heat = c->heat_per_ion * (c->G_HI * nHI + c->G_HeI * nHe * y1n + c->G_HeII * nHe * y2n) +
+                    c->heat_rate;
       double L = cooling(r, mask, nen2, nHI, nHII, nHe * y1n, nHe * y2n, nHe * y3n);
       double L1 = L / T;
       double C = ccomp * nen2;
@@ -628,6 +670,10 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
   const int nb = c->n_bins;
   or_freeze_absorbers(c);
   memset(c->budget, 0, sizeof c->budget);
+  /* periodic box: a packet travels at most c dt in the step (in cells) */
+  c->path_limit = c->periodic ? (C_LIGHT * dt) / c->dl : INFINITY;
+  if (c->periodic && !(c->path_limit <= 1073741824.0))
+    return fail(c, "periodic box: the light-travel distance of the step exceeds 2^30 cells");
 
   /* photon quantum q = 2^E with n_src * max_s(ndot_s) dt / q <= 2^62 */
   double mx = 0.0;
@@ -747,16 +793,36 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
     const double qE = ldexp(1.0, E + c->heatF) * EV;   /* erg per heat unit */
     int64_t subs = 0;
     for (int64_t i = 0; i < c->ncell; ++i) {
+      if (c->chem_stride > 1 && (uint64_t)i % c->chem_stride != 0) continue;   /* timing sample */
       or_chem_t ch;
       ch.nH = c->nH[i];
       ch.nHe = c->nH[i] * c->he_over_h;
       ch.xHII = c->xHII[i]; ch.xHeII = c->xHeII[i]; ch.xHeIII = c->xHeIII[i]; ch.T = c->T[i];
-      double NHI = c->aHI[i] * V, NHeI = c->aHeI[i] * V, NHeII = c->aHeII[i] * V;
-      ch.G_HI = NHI > 0 ? ((double)c->dHI[i] * q) / (dt * NHI) : 0.0;
-      ch.G_HeI = NHeI > 0 ? ((double)c->dHeI[i] * q) / (dt * NHeI) : 0.0;
-      ch.G_HeII = NHeII > 0 ? ((double)c->dHeII[i] * q) / (dt * NHeII) : 0.0;
-      int64_t nabs = (c->dHI[i] + c->dHeI[i]) + c->dHeII[i];
-      ch.heat_per_ion = nabs > 0 ? ((double)c->dE[i] * qE) / ((double)nabs * q) : 0.0;
+      const double dHI = (double)c->dHI[i] * c->dep_scale, dHeI = (double)c->dHeI[i] * c->dep_scale;
+      const double dHeII = (double)c->dHeII[i] * c->dep_scale, dE = (double)c->dE[i] * c->dep_scale;
+      ch.S_HI = ch.S_HeI = ch.S_HeII = 0.0;
+      ch.heat_rate = 0.0;
+      if (!c->coupling) {
+        /* photo-ionisation rate per absorber frozen at the start of the step */
+        double NHI = c->aHI[i] * V, NHeI = c->aHeI[i] * V, NHeII = c->aHeII[i] * V;
+        ch.G_HI = NHI > 0 ? (dHI * q) / (dt * NHI) : 0.0;
+        ch.G_HeI = NHeI > 0 ? (dHeI * q) / (dt * NHeI) : 0.0;
+        ch.G_HeII = NHeII > 0 ? (dHeII * q) / (dt * NHeII) : 0.0;
+        int64_t nabs = (c->dHI[i] + c->dHeI[i]) + c->dHeII[i];
+        ch.heat_per_ion = nabs > 0 ? (dE * qE) / (((double)nabs * c->dep_scale) * q) : 0.0;
+      } else {
+        /* photon-conserving: every absorbed photon ionises one atom of its
+           species, at a constant rate over the step (per atom of the element:
+           H for H I, He for He I and He II); the excess energy heats at a
+           constant rate */
+        double NH = ch.nH * V, NHe = ch.nHe * V;
+        ch.G_HI = ch.G_HeI = ch.G_HeII = 0.0;
+        ch.heat_per_ion = 0.0;
+        ch.S_HI = NH > 0 ? (dHI * q) / (dt * NH) : 0.0;
+        ch.S_HeI = NHe > 0 ? (dHeI * q) / (dt * NHe) : 0.0;
+        ch.S_HeII = NHe > 0 ? (dHeII * q) / (dt * NHe) : 0.0;
+        ch.heat_rate = (dE * qE) / (dt * V);
+      }
       /* with the diffuse field on, recombinations to the ground state are
          no longer absorbed on the spot: case A, and they are counted */
       ch.isothermal = c->isothermal; ch.caseB = c->f_rec > 0 ? 0 : c->caseB; ch.T_cmb = c->T_cmb;

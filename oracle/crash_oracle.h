@@ -44,6 +44,13 @@ typedef struct {
   uint64_t seed;
   double f_rec;                  /* > 0: diffuse recombination radiation with this
                                     re-emission threshold (Sec. 2); 0: off */
+  int coupling;                  /* transport -> chemistry: 0 = photo-ionisation rate per
+                                    frozen absorber (default); 1 = photon-conserving: the
+                                    step's absorbed photons ionise at a constant rate, the
+                                    source of a species off while it has no atoms left */
+  int periodic;                  /* 1: periodic box (Sec. 2): a packet leaving a face
+                                    re-enters at the opposite one and stops after the
+                                    distance light travels in the step, c dt */
 } or_grid_desc;
 
 typedef struct or_ctx or_ctx;
@@ -58,6 +65,11 @@ int oracle_step(or_ctx* c, double dt_s, uint64_t packets_per_step);
 int oracle_read_fields(or_ctx* c, int field_id, void* out);
 int oracle_write_fields(or_ctx* c, int field_id, const void* in);
 int oracle_set_step_index(or_ctx* c, uint64_t step);
+/* Timing sample of the per-cell update (CPU baseline only; 1 and 1.0 are
+   the full step): update only the cells whose index is a multiple of
+   chem_stride, with every deposit multiplied by dep_scale (the deposits a
+   full step would make when only a window of packet ids was traced). */
+int oracle_set_chem_sample(or_ctx* c, uint32_t chem_stride, double dep_scale);
 void oracle_free(or_ctx* c);
 const char* oracle_last_error(or_ctx* c);
 
@@ -84,6 +96,11 @@ typedef struct {
   double xHII, xHeII, xHeIII, T;
   double G_HI, G_HeI, G_HeII;       /* photoionisation rate per absorber, s^-1 */
   double heat_per_ion;              /* mean photo-electron energy per absorbed photon, erg */
+  double S_HI, S_HeI, S_HeII;       /* constant photo-ionisations per atom of the element,
+                                       s^-1 (photon-conserving coupling); each is on in a
+                                       sub-step only while its species is present at the
+                                       start of the sub-step */
+  double heat_rate;                 /* constant photo-heating, erg cm^-3 s^-1 */
   int isothermal, caseB;
   double T_cmb;                     /* <= 0: Compton off */
   double eps;                       /* relative change allowed per sub-step */

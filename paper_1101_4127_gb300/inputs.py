@@ -142,6 +142,8 @@ class Box:
     bin_frac: np.ndarray        # (n_src, n_bins)
     dims: Optional[tuple] = None  # (nx, ny, nz) for non-cubic grids; default (n, n, n)
     f_rec: float = 0.0            # > 0: diffuse recombination field with this threshold
+    coupling: int = 0             # 1: photon-conserving transport -> chemistry coupling
+    periodic: int = 0             # 1: periodic box, packets stop after the light-travel distance
 
     @property
     def n_src(self) -> int:
