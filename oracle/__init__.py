@@ -82,6 +82,8 @@ def lib():
             L.oracle_write_fields.argtypes = [P, C.c_int, P]
             L.oracle_set_step_index.argtypes = [P, C.c_uint64]
             L.oracle_set_chem_sample.argtypes = [P, C.c_uint32, C.c_double]
+            L.oracle_write_deposits.argtypes = [P, P]
+            L.oracle_chemistry.argtypes = [P, C.c_double]
             L.oracle_free.argtypes = [P]
             L.oracle_free.restype = None
             L.oracle_last_error.argtypes = [P]
@@ -252,6 +254,20 @@ class OracleGrid:
 
     def set_step_index(self, k):
         self._check(self.L.oracle_set_step_index(self.ctx, int(k)))
+
+    def read_deposits(self):
+        """Deposits as int64[cells, 4] (H I, He I, He II, heat)."""
+        return np.stack([self.read(f).reshape(-1) for f in (F_DEP_HI, F_DEP_HEI, F_DEP_HEII,
+                                                             F_DEP_E)], axis=1)
+
+    def write_deposits(self, dep):
+        a = np.ascontiguousarray(dep, np.int64).reshape(-1, 4)
+        assert a.shape[0] == self.ncell
+        self._check(self.L.oracle_write_deposits(self.ctx, a.ctypes.data_as(C.c_void_p)))
+
+    def chemistry(self, dt_s):
+        """The per-cell update of the last step, which ran without chemistry."""
+        self._check(self.L.oracle_chemistry(self.ctx, float(dt_s)))
 
     def set_chem_sample(self, stride, dep_scale=1.0):
         """Timing sample of the per-cell update (CPU baseline only)."""

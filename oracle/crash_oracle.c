@@ -61,6 +61,8 @@ struct or_ctx {
   double path_limit;                          /* periodic: c dt / dl of this step (cells) */
   uint32_t chem_stride;                       /* timing sample of the per-cell update */
   double dep_scale;
+  int chem_pending;                           /* last step ran without chemistry */
+  double last_dt;
   double *rec[3];                             /* ground-state recombination photons */
   double *nH, *xHII, *xHeII, *xHeIII, *T;
   double *aHI, *aHeI, *aHeII;                 /* frozen absorber densities */
@@ -558,10 +560,11 @@ int or_chem_cell(or_chem_t* c, double dt) {
     double IH = c->G_HI + bH * ne, RH = aH * ne;
     double I1 = c->G_HeI + bHe1 * ne, R2 = aHe2 * ne, I2 = c->G_HeII + bHe2 * ne, R3 = aHe3 * ne;
     /* constant-count photo-ionisation sources (photon-conserving coupling),
-       each on while its species is present at the start of the sub-step */
-    double sH = (1.0 - x) > 0.0 ? c->S_HI : 0.0;
-    double s1 = y1 > 0.0 ? c->S_HeI : 0.0;
-    double s2 = y2 > 0.0 ? c->S_HeII : 0.0;
+       for the step size at most what the atoms present can take over the
+       time left (a used-up species does not shorten the sub-steps) */
+    double sH = fmin(c->S_HI, (1.0 - x) / rem);
+    double s1 = fmin(c->S_HeI, y1 / rem);
+    double s2 = fmin(c->S_HeII, y2 / rem);
     double dx = (sH + IH * (1.0 - x)) - RH * x;
     double dy1 = (-I1 * y1 + R2 * y2) - s1;
     double dy3 = (s2 + I2 * y2) - R3 * y3;
@@ -588,6 +591,11 @@ int or_chem_cell(or_chem_t* c, double dt) {
       if (adT * h > c->eps * T) h = c->eps * T / adT;
     }
     if (nsub == c->max_sub - 1 || !(h < rem)) h = rem;
+    /* the sources of the sub-step ionise at most the atoms present (He II
+       also what He I gives it): the photons beyond are lost */
+    sH = fmin(c->S_HI, (1.0 - x) / h);
+    s1 = fmin(c->S_HeI, y1 / h);
+    s2 = fmin(c->S_HeII, y2 / h + s1);
     /* backward Euler with n_e from the end of the sub-step */
     double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
     for (int it = 0; it < 4; ++it) {
@@ -659,6 +667,59 @@ int or_chem_cell(or_chem_t* c, double dt) {
   return nsub;
 }
 
+/* The per-cell update of a step (Sec. 2 network and continuous processes,
+   sub-sampled as in Sec. 3.2) from the deposits the context holds, with the
+   step's photon quantum 2^E. */
+static void or_step_chemistry(or_ctx* c, double dt, int E) {
+  const double V = (c->dl * c->dl) * c->dl;
+  const double q = ldexp(1.0, E);
+  const double qE = ldexp(1.0, E + c->heatF) * EV;   /* erg per heat unit */
+  int64_t subs = 0;
+  for (int64_t i = 0; i < c->ncell; ++i) {
+    if (c->chem_stride > 1 && (uint64_t)i % c->chem_stride != 0) continue;   /* timing sample */
+    or_chem_t ch;
+    ch.nH = c->nH[i];
+    ch.nHe = c->nH[i] * c->he_over_h;
+    ch.xHII = c->xHII[i]; ch.xHeII = c->xHeII[i]; ch.xHeIII = c->xHeIII[i]; ch.T = c->T[i];
+    const double dHI = (double)c->dHI[i] * c->dep_scale, dHeI = (double)c->dHeI[i] * c->dep_scale;
+    const double dHeII = (double)c->dHeII[i] * c->dep_scale, dE = (double)c->dE[i] * c->dep_scale;
+    ch.S_HI = ch.S_HeI = ch.S_HeII = 0.0;
+    ch.heat_rate = 0.0;
+    if (!c->coupling) {
+      /* photo-ionisation rate per absorber frozen at the start of the step */
+      double NHI = c->aHI[i] * V, NHeI = c->aHeI[i] * V, NHeII = c->aHeII[i] * V;
+      ch.G_HI = NHI > 0 ? (dHI * q) / (dt * NHI) : 0.0;
+      ch.G_HeI = NHeI > 0 ? (dHeI * q) / (dt * NHeI) : 0.0;
+      ch.G_HeII = NHeII > 0 ? (dHeII * q) / (dt * NHeII) : 0.0;
+      int64_t nabs = (c->dHI[i] + c->dHeI[i]) + c->dHeII[i];
+      ch.heat_per_ion = nabs > 0 ? (dE * qE) / (((double)nabs * c->dep_scale) * q) : 0.0;
+    } else {
+      /* photon-conserving: every absorbed photon ionises one atom of its
+         species, at a constant rate over the step (per atom of the element:
+         H for H I, He for He I and He II); the excess energy heats at a
+         constant rate */
+      double NH = ch.nH * V, NHe = ch.nHe * V;
+      ch.G_HI = ch.G_HeI = ch.G_HeII = 0.0;
+      ch.heat_per_ion = 0.0;
+      ch.S_HI = NH > 0 ? (dHI * q) / (dt * NH) : 0.0;
+      ch.S_HeI = NHe > 0 ? (dHeI * q) / (dt * NHe) : 0.0;
+      ch.S_HeII = NHe > 0 ? (dHeII * q) / (dt * NHe) : 0.0;
+      ch.heat_rate = (dE * qE) / (dt * V);
+    }
+    /* with the diffuse field on, recombinations to the ground state are
+       no longer absorbed on the spot: case A, and they are counted */
+    ch.isothermal = c->isothermal; ch.caseB = c->f_rec > 0 ? 0 : c->caseB; ch.T_cmb = c->T_cmb;
+    ch.eps = c->chem_eps; ch.max_sub = c->chem_max_sub; ch.cool_mask = c->cool_mask;
+    ch.count_rec = c->f_rec > 0;
+    ch.rec[0] = ch.rec[1] = ch.rec[2] = 0.0;
+    subs += or_chem_cell(&ch, dt);
+    c->xHII[i] = ch.xHII; c->xHeII[i] = ch.xHeII; c->xHeIII[i] = ch.xHeIII; c->T[i] = ch.T;
+    if (ch.count_rec)
+      for (int a = 0; a < 3; ++a) c->rec[a][i] += ch.rec[a] * V;
+  }
+  c->budget[7] = subs;
+}
+
 /* ------------------------------------------------------------ one step */
 int oracle_step(or_ctx* c, double dt, uint64_t P) {
   if (!c) return -1;
@@ -672,13 +733,14 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
   memset(c->budget, 0, sizeof c->budget);
   /* periodic box: a packet travels at most c dt in the step (in cells) */
   c->path_limit = c->periodic ? (C_LIGHT * dt) / c->dl : INFINITY;
-  if (c->periodic && !(c->path_limit <= 1073741824.0))
-    return fail(c, "periodic box: the light-travel distance of the step exceeds 2^30 cells");
+  if (c->periodic && !(c->path_limit <= 536870912.0))
+    return fail(c, "periodic box: the light-travel distance of the step exceeds 2^29 cells");
 
-  /* photon quantum q = 2^E with n_src * max_s(ndot_s) dt / q <= 2^62 */
-  double mx = 0.0;
-  for (int s = 0; s < c->n_src; ++s) if (c->ndot[s] > mx) mx = c->ndot[s];
-  double X = ((double)c->n_src * mx) * dt;
+  /* photon quantum q = 2^E with the step's photons of all sources,
+     (sum_s ndot_s) dt / q, at most 2^62 (the sum taken in source order) */
+  double tot = 0.0;
+  for (int s = 0; s < c->n_src; ++s) tot += c->ndot[s];
+  double X = tot * dt;
   int E = X > 0 ? ceil_log2(X) - 62 : 0;
   if (c->f_rec > 0) {
     /* the diffuse field re-emits this step at most ncell times the largest
@@ -709,7 +771,7 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
   int64_t Bj[OR_MAX_BINS], N[OR_MAX_BINS];
   for (int s = 0; s < c->n_src; ++s) {
     /* the source's photons this step in quanta, split over bins by the
-       cumulative SED fractions, the last bin taking the remainder */
+     cumulative SED fractions, the last bin taking the remainder */
     int64_t B = llrint(ldexp(c->ndot[s] * dt, -E));
     double F = 0.0;
     int64_t prev = 0;
@@ -729,7 +791,7 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
     for (uint32_t p = pb; p < pe; ++p) {
       double d[3];
       if (or_direction(c->seed, (uint32_t)c->step, (uint32_t)s, p, d) < 0)
-        return fail(c, "direction sampling exceeded 64 attempts");
+      return fail(c, "direction sampling exceeded 64 attempts");
       for (int j = 0; j < nb; ++j) {
         int64_t base = Bj[j] / (int64_t)Ns, rmd = Bj[j] % (int64_t)Ns;
         N[j] = base + ((int64_t)p < rmd ? 1 : 0);
@@ -743,40 +805,40 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
   }
   if (c->f_rec > 0) {
     /* diffuse recombination radiation (Sec. 2): every cell where the
-       recombinations to the ground state of some species reach f_rec times
-       that element's atoms in the cell re-emits them as one packet, and the
-       species' count restarts from zero.  The photons of a species go to the
-       lowest bin at or above its ionisation threshold (its Milne spectrum
-       lies within a few kT of the threshold); in quanta q of this step. */
+     recombinations to the ground state of some species reach f_rec times
+     that element's atoms in the cell re-emits them as one packet, and the
+     species' count restarts from zero.  The photons of a species go to the
+     lowest bin at or above its ionisation threshold (its Milne spectrum
+     lies within a few kT of the threshold); in quanta q of this step. */
     const double V = (c->dl * c->dl) * c->dl;
     const double q = ldexp(1.0, E);
     int rec_bin[3];
     for (int a = 0; a < 3; ++a) {
       rec_bin[a] = -1;
       for (int j = 0; j < nb; ++j)
-        if (c->binE[j] >= E_TH[a] && (rec_bin[a] < 0 || c->binE[j] < c->binE[rec_bin[a]]))
-          rec_bin[a] = j;
+      if (c->binE[j] >= E_TH[a] && (rec_bin[a] < 0 || c->binE[j] < c->binE[rec_bin[a]]))
+        rec_bin[a] = j;
     }
     for (int64_t i = 0; i < c->ncell; ++i) {
       const double atoms[3] = {c->nH[i] * V, c->nH[i] * c->he_over_h * V,
-                               c->nH[i] * c->he_over_h * V};
+                             c->nH[i] * c->he_over_h * V};
       int64_t Nq[3] = {0, 0, 0};
       int any = 0;
       for (int a = 0; a < 3; ++a)
-        if (atoms[a] > 0 && c->rec[a][i] > 0 && c->rec[a][i] >= c->f_rec * atoms[a]) {
-          Nq[a] = llrint(c->rec[a][i] / q);
-          c->rec[a][i] = 0.0;
-          any = 1;
-        }
+      if (atoms[a] > 0 && c->rec[a][i] > 0 && c->rec[a][i] >= c->f_rec * atoms[a]) {
+        Nq[a] = llrint(c->rec[a][i] / q);
+        c->rec[a][i] = 0.0;
+        any = 1;
+      }
       if (!any) continue;
       for (int j = 0; j < nb; ++j) N[j] = 0;
       int64_t tot = 0;
       for (int a = 0; a < 3; ++a)
-        if (rec_bin[a] >= 0 && Nq[a] > 0) { N[rec_bin[a]] += Nq[a]; tot += Nq[a]; }
+      if (rec_bin[a] >= 0 && Nq[a] > 0) { N[rec_bin[a]] += Nq[a]; tot += Nq[a]; }
       if (tot == 0) continue;
       double pos[3], d[3];
       if (or_rec_start(c->seed, (uint32_t)c->step, i, c->nx, c->ny, pos, d) < 0)
-        return fail(c, "direction sampling exceeded 64 attempts");
+      return fail(c, "direction sampling exceeded 64 attempts");
       emitted += tot;
       int64_t cr = or_trace_packet(c, pos, d, N, &escaped, &absorbed, 0, NULL, NULL, NULL);
       if (cr < 0) return -1;
@@ -787,55 +849,9 @@ int oracle_step(or_ctx* c, double dt, uint64_t P) {
   c->budget[0] = emitted; c->budget[1] = absorbed; c->budget[2] = escaped;
   c->budget[3] = crossings; c->budget[4] = traced;
 
-  if (c->chemistry) {
-    const double V = (c->dl * c->dl) * c->dl;
-    const double q = ldexp(1.0, E);
-    const double qE = ldexp(1.0, E + c->heatF) * EV;   /* erg per heat unit */
-    int64_t subs = 0;
-    for (int64_t i = 0; i < c->ncell; ++i) {
-      if (c->chem_stride > 1 && (uint64_t)i % c->chem_stride != 0) continue;   /* timing sample */
-      or_chem_t ch;
-      ch.nH = c->nH[i];
-      ch.nHe = c->nH[i] * c->he_over_h;
-      ch.xHII = c->xHII[i]; ch.xHeII = c->xHeII[i]; ch.xHeIII = c->xHeIII[i]; ch.T = c->T[i];
-      const double dHI = (double)c->dHI[i] * c->dep_scale, dHeI = (double)c->dHeI[i] * c->dep_scale;
-      const double dHeII = (double)c->dHeII[i] * c->dep_scale, dE = (double)c->dE[i] * c->dep_scale;
-      ch.S_HI = ch.S_HeI = ch.S_HeII = 0.0;
-      ch.heat_rate = 0.0;
-      if (!c->coupling) {
-        /* photo-ionisation rate per absorber frozen at the start of the step */
-        double NHI = c->aHI[i] * V, NHeI = c->aHeI[i] * V, NHeII = c->aHeII[i] * V;
-        ch.G_HI = NHI > 0 ? (dHI * q) / (dt * NHI) : 0.0;
-        ch.G_HeI = NHeI > 0 ? (dHeI * q) / (dt * NHeI) : 0.0;
-        ch.G_HeII = NHeII > 0 ? (dHeII * q) / (dt * NHeII) : 0.0;
-        int64_t nabs = (c->dHI[i] + c->dHeI[i]) + c->dHeII[i];
-        ch.heat_per_ion = nabs > 0 ? (dE * qE) / (((double)nabs * c->dep_scale) * q) : 0.0;
-      } else {
-        /* photon-conserving: every absorbed photon ionises one atom of its
-           species, at a constant rate over the step (per atom of the element:
-           H for H I, He for He I and He II); the excess energy heats at a
-           constant rate */
-        double NH = ch.nH * V, NHe = ch.nHe * V;
-        ch.G_HI = ch.G_HeI = ch.G_HeII = 0.0;
-        ch.heat_per_ion = 0.0;
-        ch.S_HI = NH > 0 ? (dHI * q) / (dt * NH) : 0.0;
-        ch.S_HeI = NHe > 0 ? (dHeI * q) / (dt * NHe) : 0.0;
-        ch.S_HeII = NHe > 0 ? (dHeII * q) / (dt * NHe) : 0.0;
-        ch.heat_rate = (dE * qE) / (dt * V);
-      }
-      /* with the diffuse field on, recombinations to the ground state are
-         no longer absorbed on the spot: case A, and they are counted */
-      ch.isothermal = c->isothermal; ch.caseB = c->f_rec > 0 ? 0 : c->caseB; ch.T_cmb = c->T_cmb;
-      ch.eps = c->chem_eps; ch.max_sub = c->chem_max_sub; ch.cool_mask = c->cool_mask;
-      ch.count_rec = c->f_rec > 0;
-      ch.rec[0] = ch.rec[1] = ch.rec[2] = 0.0;
-      subs += or_chem_cell(&ch, dt);
-      c->xHII[i] = ch.xHII; c->xHeII[i] = ch.xHeII; c->xHeIII[i] = ch.xHeIII; c->T[i] = ch.T;
-      if (ch.count_rec)
-        for (int a = 0; a < 3; ++a) c->rec[a][i] += ch.rec[a] * V;
-    }
-    c->budget[7] = subs;
-  }
+  c->chem_pending = !c->chemistry;
+  c->last_dt = dt;
+  if (c->chemistry) or_step_chemistry(c, dt, E);
   c->step += 1;
   return 0;
 }
@@ -876,4 +892,27 @@ int oracle_write_fields(or_ctx* c, int f, const void* in) {
       return 0;
     default: return fail(c, "field is not writable");
   }
+}
+
+/* The exchange of a step split over processes: overwrite the deposits
+   (int64[cells][4]: H I, He I, He II, heat) with those summed over the
+   processes, then run the per-cell update of the last step, which must have
+   run without chemistry (same shapes as the library's crash_write_deposits
+   and crash_chemistry). */
+int oracle_write_deposits(or_ctx* c, const int64_t* in) {
+  if (!c || !in) return -1;
+  for (int64_t i = 0; i < c->ncell; ++i) {
+    c->dHI[i] = in[4 * i]; c->dHeI[i] = in[4 * i + 1];
+    c->dHeII[i] = in[4 * i + 2]; c->dE[i] = in[4 * i + 3];
+  }
+  return 0;
+}
+
+int oracle_chemistry(or_ctx* c, double dt) {
+  if (!c) return -1;
+  if (!c->chem_pending) return fail(c, "the last step ran its chemistry already");
+  if (!(dt == c->last_dt)) return fail(c, "chemistry needs the dt of its step");
+  or_step_chemistry(c, dt, (int)c->budget[5]);
+  c->chem_pending = 0;
+  return 0;
 }

@@ -46,8 +46,8 @@ typedef struct {
                                     re-emission threshold (Sec. 2); 0: off */
   int coupling;                  /* transport -> chemistry: 0 = photo-ionisation rate per
                                     frozen absorber (default); 1 = photon-conserving: the
-                                    step's absorbed photons ionise at a constant rate, the
-                                    source of a species off while it has no atoms left */
+                                    step's absorbed photons ionise at a constant rate, at
+                                    most the atoms present; the rest are lost */
   int periodic;                  /* 1: periodic box (Sec. 2): a packet leaving a face
                                     re-enters at the opposite one and stops after the
                                     distance light travels in the step, c dt */
@@ -70,6 +70,11 @@ int oracle_set_step_index(or_ctx* c, uint64_t step);
    chem_stride, with every deposit multiplied by dep_scale (the deposits a
    full step would make when only a window of packet ids was traced). */
 int oracle_set_chem_sample(or_ctx* c, uint32_t chem_stride, double dep_scale);
+/* exchange of a step split over processes (the library's crash_write_deposits
+   and crash_chemistry): deposits int64[cells][4], then the per-cell update
+   of the last step, run without chemistry, with that step's dt */
+int oracle_write_deposits(or_ctx* c, const int64_t* in);
+int oracle_chemistry(or_ctx* c, double dt_s);
 void oracle_free(or_ctx* c);
 const char* oracle_last_error(or_ctx* c);
 
@@ -97,9 +102,8 @@ typedef struct {
   double G_HI, G_HeI, G_HeII;       /* photoionisation rate per absorber, s^-1 */
   double heat_per_ion;              /* mean photo-electron energy per absorbed photon, erg */
   double S_HI, S_HeI, S_HeII;       /* constant photo-ionisations per atom of the element,
-                                       s^-1 (photon-conserving coupling); each is on in a
-                                       sub-step only while its species is present at the
-                                       start of the sub-step */
+                                       s^-1 (photon-conserving coupling); in a sub-step each
+                                       ionises at most the atoms of its species present */
   double heat_rate;                 /* constant photo-heating, erg cm^-3 s^-1 */
   int isothermal, caseB;
   double T_cmb;                     /* <= 0: Compton off */

@@ -20,11 +20,17 @@ C_LIGHT = 2.99792458e10
 def test_constant_count_source_closed_forms():
     """With only the constant source on (no recombination, no collisions,
     fixed T) the fractions move linearly: x = x0 + S t until the species is
-    used up, then the source stops (clamped at zero neutrals)."""
+    used up, then stay clamped at zero neutrals."""
     st, n = oracle.chem_cell(5e13, nH=1e-3, xHII=0.1, T=1e4, S_HI=1e-14, isothermal=1, cool_mask=0)
     assert st["xHII"] == pytest.approx(0.6, rel=1e-12, abs=0)
     st, n = oracle.chem_cell(2e14, nH=1e-3, xHII=0.1, T=1e4, S_HI=1e-14, isothermal=1, cool_mask=0)
-    assert st["xHII"] == 1.0 and n < 100
+    assert st["xHII"] == 1.0
+    # He I used up by its source: He III keeps its share, the excess photons
+    # are lost (no sub-steps are spent on the used-up species)
+    st, n = oracle.chem_cell(1e14, nH=1e-3, nHe=1e-4, xHII=1.0, xHeII=0.3, xHeIII=0.1, T=2e4,
+                             S_HeI=1e-13, isothermal=1, cool_mask=0)
+    assert 1 - st["xHeII"] - st["xHeIII"] < 1e-15
+    assert st["xHeIII"] == pytest.approx(0.1, rel=1e-12, abs=0) and n < 100
     # helium: He I -> He II at S1, He II -> He III at S2 (both present throughout)
     st, _ = oracle.chem_cell(1e13, nH=1e-3, nHe=1e-4, xHII=1.0, xHeII=0.3, xHeIII=0.1, T=2e4,
                              S_HeI=2e-14, S_HeII=1e-14, isothermal=1, cool_mask=0)

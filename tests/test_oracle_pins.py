@@ -267,8 +267,8 @@ def test_photon_budget_closes_exactly():
                + g.read(oracle.F_DEP_HEII).sum())
         assert dep == b[1]
         assert b[4] == 2100 and b[3] > 0
-        # per-step quantum: n_src max(ndot) dt / 2^E in (2^61, 2^62]
-        X = 3 * ndot.max() * dt / 2.0 ** b[5]
+        # per-step quantum: the step's photons of all sources, sum(ndot) dt / 2^E, in (2^61, 2^62]
+        X = ndot.sum() * dt / 2.0 ** b[5]
         assert 2.0**61 < X <= 2.0**62
         # every source's photons are emitted, in quanta
         assert abs(b[0] - sum(round(nd * dt / 2.0 ** b[5]) for nd in ndot)) <= 3

@@ -1,9 +1,12 @@
 """Sharding the step across ranks (CPU, gloo, world size 2): each rank
-traces a disjoint window of packet ids of every source, the int64 deposits
-are summed with an all-reduce, and the result equals one rank tracing every
-packet, bit for bit.  This is the exchange a multi-device step would make
+traces a disjoint window of packet ids of every source (sharding.
+packet_windows), the int64 deposits are summed with an all-reduce, every rank
+writes the sum back and runs the per-cell update of the step, and the
+result equals one rank tracing every packet, bit for bit: deposits, budget
+and the four state fields.  This is the exchange a multi-device step makes
 before the per-cell chemistry (packets are independent given the frozen
-absorbers; integer sums do not depend on the order or the split)."""
+absorbers; integer sums do not depend on the order or the split); the CUDA
+library takes the same calls (crash_write_deposits, crash_chemistry)."""
 import os
 import socket
 
@@ -36,25 +39,26 @@ def _case():
     return oracle, inputs, box, 3 * 600, 0.02 * inputs.MYR_S
 
 
-def _deposits(g, oracle):
-    return np.stack([g.read(f).reshape(-1) for f in (oracle.F_DEP_HI, oracle.F_DEP_HEI,
-                                                     oracle.F_DEP_HEII, oracle.F_DEP_E)])
-
-
 def _rank(rank, world, port, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1101_4127_gb300 import sharding
     oracle, inputs, box, P, dt = _case()
-    Ns = P // box.n_src
-    lo, hi = rank * Ns // world, (rank + 1) * Ns // world
+    lo, hi = sharding.packet_windows(P // box.n_src, world)[rank]
     g = oracle.OracleGrid.from_box(box)
     g.set_options(chemistry=0, pkt_begin=lo, pkt_end=hi)
     g.step(dt, P)
-    dep = torch.from_numpy(_deposits(g, oracle))
+    dep = torch.from_numpy(g.read_deposits())
     bud = torch.from_numpy(g.read(oracle.F_BUDGET)[:5].copy())
     dist.all_reduce(dep, op=dist.ReduceOp.SUM)
     dist.all_reduce(bud, op=dist.ReduceOp.SUM)
+    # every rank: the summed deposits, then the step's per-cell update
+    g.write_deposits(dep.numpy())
+    g.chemistry(dt)
+    state = np.stack([g.read(f).reshape(-1) for f in (oracle.F_XHII, oracle.F_XHEII,
+                                                      oracle.F_XHEIII, oracle.F_T)])
+    np.save(out + f".state{rank}.npy", state)
     if rank == 0:
         np.save(out + ".dep.npy", dep.numpy())
         np.save(out + ".bud.npy", bud.numpy())
@@ -68,7 +72,10 @@ def test_two_ranks_all_reduced_deposits_equal_single_run(tmp_path):
                        start_method="spawn")
     oracle, inputs, box, P, dt = _case()
     g = oracle.OracleGrid.from_box(box)
-    g.set_options(chemistry=0)
     g.step(dt, P)
-    assert np.array_equal(np.load(out + ".dep.npy"), _deposits(g, oracle))
+    assert np.array_equal(np.load(out + ".dep.npy"), g.read_deposits())
     assert np.array_equal(np.load(out + ".bud.npy"), g.read(oracle.F_BUDGET)[:5])
+    state = np.stack([g.read(f).reshape(-1) for f in (oracle.F_XHII, oracle.F_XHEII,
+                                                      oracle.F_XHEIII, oracle.F_T)])
+    for r in range(2):
+        assert np.array_equal(np.load(out + f".state{r}.npy"), state), r
