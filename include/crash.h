@@ -24,8 +24,9 @@
  *     CRASH_ERR_TIMEOUT result leaves the context usable only for
  *     crash_read_fields and crash_free.
  *   - The transported photons are integers in units of a per-step quantum
- *     q = 2^E (E chosen per box and step so that n_src * max(ndot) * dt / q
- *     <= 2^62), so emitted = absorbed + escaped holds exactly.
+ *     q = 2^E (E chosen per box and step so that the step's photons of all
+ *     the box's sources, sum(ndot) * dt / q, are at most 2^62), so emitted =
+ *     absorbed + escaped holds exactly.
  */
 #ifndef CRASH_H
 #define CRASH_H
@@ -96,6 +97,21 @@ typedef struct {
                                 quantum of the step also keeps (cells of the box) x (largest
                                 count over its threshold) below 2^62 quanta, and then takes
                                 one more bit, so sources plus re-emission fit in int64. */
+  int coupling;              /* transport -> chemistry (Sec. 2 couples the absorbed photons to
+                                the network; the form is a reading):
+                                0 = photo-ionisation rate per absorber frozen at the start of
+                                the step, Gamma_s = dep_s q / (dt n_s V) (default);
+                                1 = photon-conserving: the step's absorbed photons ionise at a
+                                constant rate, dep_s q / (dt V) atoms per cm^3 and s, in
+                                each chemistry sub-step at most the atoms of the species
+                                present (the photons beyond are lost); photo-heating at the
+                                deposited rate. */
+  int periodic;              /* 1: periodic box (Sec. 2): a packet crossing a face re-enters
+                                through the opposite one; its walk ends after the distance
+                                light travels in the step, c dt (at most 2^29 cells), and
+                                what it still holds then is counted as escaped.  Periodic
+                                boxes trace every packet to its end in its own thread (the
+                                mixed form's wavefront keeps no path budget). */
 } crash_grid_desc;
 
 /* Run options (crash_default_opts fills the defaults). */
@@ -128,6 +144,16 @@ typedef struct {
                                 0 = Morton (Z) curve, 1 = Hilbert curve; tile passes
                                 (tile = 1) always key by Morton tiles.  Results do not
                                 depend on it (only the order packets are traced in). */
+  int chunk_packets;         /* mixed form: packets per wavefront chunk (0 = 2^28); a step
+                                with more packets runs chunk after chunk through one queue.
+                                Results do not depend on it. */
+  int persistent;            /* mixed form, wavefront without tiles: 1 = the whole transport
+                                of a step in one cooperative launch whose blocks stay
+                                resident and meet at grid barriers between passes and
+                                re-sort phases (default); 0 = one launch per pass and per
+                                re-sort phase.  Every barrier wait is bounded (30 s), after
+                                which the step reports CRASH_ERR_TIMEOUT.  Results do not
+                                depend on it. */
 } crash_run_opts;
 
 void crash_default_opts(crash_run_opts* o);
@@ -157,6 +183,9 @@ crash_status crash_add_sources_box(crash_ctx* ctx, int box, int n_src, const dou
                                    const double* bin_frac);
 
 crash_status crash_set_options(crash_ctx* ctx, const crash_run_opts* opts);
+/* Copy the context's current options (after crash_autotune: the chosen ones)
+   to *opts. */
+crash_status crash_get_options(crash_ctx* ctx, crash_run_opts* opts);
 
 /* One time step of length dt_s (Sec. 2 and Sec. 3.2): every box emits
    packets_per_step packets split equally over its sources (must be a
@@ -207,14 +236,42 @@ int64_t crash_launch_count(crash_ctx* ctx);
 
 /* Autotuner: times transport-only trial steps over block size, crossings
    per pass, re-sort interval, register cap and tile passes (mixed form) on
-   the current state, over a window of about 2^26 packet ids, then the
-   fastest once more with Hilbert-ordered re-sort keys; the state, the
-   diffuse field's counts and the step index are restored afterwards.
-   Stores the fastest in the context's options and returns the chosen values
-   (outputs may be NULL). */
+   the current state, over a window of about 2^26 packet ids, one launch
+   per pass; then the fastest once more with Hilbert-ordered re-sort keys,
+   and the fastest of those once more as one persistent launch per step
+   (opts.persistent); the state, the diffuse field's counts and the step
+   index are restored afterwards.  Stores the fastest in the context's
+   options (persistent included) and returns the chosen values (outputs may
+   be NULL). */
 crash_status crash_autotune(crash_ctx* ctx, double dt_s, const uint64_t* packets_per_box,
                             int* block_size, int* seg_per_iter, int* resort_interval,
                             int* reg_cap, int* tile, int* sort_curve);
+
+/* ---- The exchange of a step split over several processes or GPUs.
+   Packets are independent given the frozen absorbers (Sec. 2), so a step
+   may be split by packet ids: every process holds a replica of the grid and
+   traces a window of packet ids of every source (opts.pkt_begin/pkt_end,
+   opts.chemistry = 0); the int64 deposits of all processes are summed (the
+   one exchange of the step: Sec. 2's "reduction" strategy); then each
+   process runs the per-cell update on the summed deposits.  Integer sums do
+   not depend on their order, so the result is the same bits as one process
+   tracing every packet, for any split.
+
+   Device address of the deposits of box `box`: uint64[cells][4] (H I, He I,
+   He II, heat) in the context's stream order; valid until crash_free.  A
+   step's prep zeroes them; an in-place sum (e.g. an NCCL int64 all-reduce on
+   crash_stream's stream, or after crash_sync) goes between the
+   transport-only step and crash_chemistry.  n_cells may be NULL. */
+crash_status crash_deposits_device(crash_ctx* ctx, int box, void** dev_ptr, int64_t* n_cells);
+/* Host copies of the same array: read (int64[cells][4], synchronises) and
+   overwrite (e.g. with the deposits summed over processes). */
+crash_status crash_read_deposits(crash_ctx* ctx, int box, int64_t* host_out);
+crash_status crash_write_deposits(crash_ctx* ctx, int box, const int64_t* host_in);
+/* The per-cell update (Sec. 2; sub-sampled as in Sec. 3.2) of the last
+   step, on the deposits the context now holds.  Only after a step run with
+   opts.chemistry = 0, once, and with that step's dt_s (CRASH_ERR_STATE /
+   CRASH_ERR_ARG otherwise).  Asynchronous on the context stream. */
+crash_status crash_chemistry(crash_ctx* ctx, double dt_s);
 
 crash_status crash_free(crash_ctx* ctx);
 const char* crash_last_error(crash_ctx* ctx);   /* NULL ctx: last creation error */

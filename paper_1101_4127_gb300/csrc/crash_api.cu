@@ -72,8 +72,12 @@ struct crash_ctx {
   // options / state
   crash_run_opts opts{};
   uint64_t step_host = 0;
-  bool any_he = false, any_heat = false;
+  bool any_he = false, any_heat = false, any_periodic = false;
   std::string error;
+  // exchange of a split step: the last step ran without chemistry and its
+  // per-cell update is still due (crash_chemistry), with that step's dt
+  bool chem_pending = false;
+  double last_dt = 0.0;
   // timing
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   int ev_used = 0;
@@ -132,6 +136,7 @@ extern "C" void crash_default_opts(crash_run_opts* o) {
   o->wavefront = 1;
   o->use_graph = 0;
   o->timing = 0;
+  o->persistent = 1;
 }
 
 // ---------------------------------------------------------------- teardown
@@ -185,6 +190,8 @@ static crash_status validate_desc(const crash_grid_desc& d, int i) {
     return set_err(c, CRASH_ERR_OVERFLOW, "grid too large");
   if (!d.T && !(d.T0 > 0)) return set_err(c, CRASH_ERR_ARG, "T0 must be positive");
   if (!(d.f_rec >= 0 && d.f_rec <= 1)) return set_err(c, CRASH_ERR_ARG, "f_rec must be in [0, 1]");
+  if (d.coupling != 0 && d.coupling != 1) return set_err(c, CRASH_ERR_ARG, "coupling must be 0 or 1");
+  if (d.periodic != 0 && d.periodic != 1) return set_err(c, CRASH_ERR_ARG, "periodic must be 0 or 1");
   return CRASH_OK;
 }
 
@@ -256,7 +263,10 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
     m.caseB = d.caseB ? 1 : 0;
     m.max_iter = d.nx + d.ny + d.nz + 3;
     m.f_rec = d.f_rec;
+    m.coupling = d.coupling;
+    m.periodic = d.periodic;
     c->any_rec |= d.f_rec > 0;
+    c->any_periodic |= d.periodic != 0;
     off += m.ncell;
     c->any_he |= d.he_over_h > 0;
     c->any_heat |= !d.isothermal;
@@ -470,7 +480,6 @@ extern "C" crash_status crash_add_sources_box(crash_ctx* c, int box, int n_src,
   if (others && (n_bins != c->n_bins || !std::equal(bin_eV, bin_eV + n_bins, c->bin_eV.begin())))
     return set_err(c, CRASH_ERR_ARG, "all boxes must use the same frequency bins");
   const crash_grid_desc& d = c->bh[box].d;
-  double mx = 0.0;
   for (int s = 0; s < n_src; ++s) {
     const double* p = pos + 3 * s;
     if (!(p[0] >= 0 && p[0] < d.nx && p[1] >= 0 && p[1] < d.ny && p[2] >= 0 && p[2] < d.nz))
@@ -480,7 +489,6 @@ extern "C" crash_status crash_add_sources_box(crash_ctx* c, int box, int n_src,
     for (int j = 0; j < n_bins; ++j)
       if (!(bin_frac[(size_t)s * n_bins + j] >= 0))
         return set_err(c, CRASH_ERR_ARG, "bin fractions must be >= 0");
-    mx = std::max(mx, ndot[s]);
   }
   BoxHost& h = c->bh[box];
   h.pos.assign(pos, pos + 3 * n_src);
@@ -501,7 +509,9 @@ extern "C" crash_status crash_add_sources_box(crash_ctx* c, int box, int n_src,
         c->rec_bin[sp] = j;
   }
   for (int b = 0; b < c->n_boxes; ++b) c->meta[b].heatF = heatF;
-  c->meta[box].ndot_max = mx;
+  double sum = 0.0;                       // in source order, as the specification sums
+  for (int s = 0; s < n_src; ++s) sum += ndot[s];
+  c->meta[box].ndot_sum = sum;
   crash_status st = rebuild_sources(c);
   if (st != CRASH_OK) return st;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
@@ -522,8 +532,15 @@ extern "C" crash_status crash_set_options(crash_ctx* c, const crash_run_opts* o)
   if (o->block_size < 0 || o->block_size > 1024 || (o->block_size % 32))
     return set_err(c, CRASH_ERR_ARG, "block_size must be a multiple of 32 in [0, 1024]");
   if (o->seg_per_iter < 0) return set_err(c, CRASH_ERR_ARG, "seg_per_iter must be >= 0");
+  if (o->chunk_packets < 0) return set_err(c, CRASH_ERR_ARG, "chunk_packets must be >= 0");
   c->opts = *o;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_get_options(crash_ctx* c, crash_run_opts* o) {
+  if (!c || !o) return set_err(c, CRASH_ERR_ARG, "NULL argument");
+  *o = c->opts;
   return CRASH_OK;
 }
 
@@ -603,6 +620,8 @@ static StepArgs make_args(crash_ctx* c, double dt, int64_t total) {
   a.max_tiles = c->max_tiles;
   a.err = c->err;
   a.any_he = c->any_he; a.any_heat = c->any_heat;
+  a.any_periodic = c->any_periodic;
+  a.max_iter_step = c->max_iter;
   a.chemistry = c->opts.chemistry;
   a.fp32_rates = c->precision == CRASH_MIXED;
   a.chem_eps = c->opts.chem_eps;
@@ -647,7 +666,7 @@ static crash_status enqueue_step(crash_ctx* c, const StepArgs& a, bool timing, i
       // option applies to the bucket keys of the other passes only
       crash_run_opts o = c->opts;
       if (o.tile) o.sort_curve = 0;
-      int rc = launch_trace_mixed(a, c->tables, o, c->wf, c->max_iter, c->stream,
+      int rc = launch_trace_mixed(a, c->tables, o, c->wf, a.max_iter_step, c->stream,
                                   timing ? &c->events : nullptr, &c->ev_used);
       if (rc < 0) return set_err(c, CRASH_ERR_CUDA, "mixed transport launch failed");
       *nk += rc;
@@ -717,6 +736,20 @@ extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t
     key.push_back(P[b]);
   }
   if (total > ((int64_t)1 << 40)) return set_err(c, CRASH_ERR_OVERFLOW, "too many packets in one step");
+  // DDA bound of this step: a periodic box's packets travel c dt, so their
+  // walks are bounded by 2 L + 4 face crossings (L = c dt / dl cells)
+  int step_max_iter = c->max_iter;
+  for (int b = 0; b < c->n_boxes; ++b) {
+    BoxMeta& m = c->meta[b];
+    if (!m.periodic) continue;
+    const double L = (CRASH_C_LIGHT * dt) / m.dl;
+    if (!(L <= 536870912.0))
+      return set_err(c, CRASH_ERR_ARG, "periodic box: c dt exceeds 2^29 cells");
+    m.max_iter = (int)(2.0 * L) + 4;
+    m.path_cells32 = (float)L;
+    step_max_iter = std::max(step_max_iter, m.max_iter);
+    key.push_back((uint64_t)m.max_iter);
+  }
   CK(cudaMemcpyAsync(c->d_meta, c->meta.data(), sizeof(BoxMeta) * c->n_boxes,
                      cudaMemcpyHostToDevice, c->stream));
   if (c->precision == CRASH_MIXED) {
@@ -725,7 +758,8 @@ extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t
     // thread.  Larger chunks put more packets in each sort bucket of a pass,
     // so more crossings of a cell fall close together in time and its
     // deposit record is reused in L2.
-    const int64_t want = c->opts.wavefront ? std::min<int64_t>(total, (int64_t)1 << 28) : 0;
+    const int64_t chunk = c->opts.chunk_packets > 0 ? (int64_t)c->opts.chunk_packets : (int64_t)1 << 28;
+    const int64_t want = (c->opts.wavefront && !c->any_periodic) ? std::min<int64_t>(total, chunk) : 0;
     if (c->wf && (c->wf_mode != c->opts.wavefront || wavefront_capacity(c->wf) < want)) {
       CK(cudaStreamSynchronize(c->stream));
       wavefront_destroy(c->wf);
@@ -744,6 +778,7 @@ extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t
     }
   }
   StepArgs a = make_args(c, dt, total);
+  a.max_iter_step = step_max_iter;
   const bool timing = c->opts.timing != 0;
   crash_status st;
   if (c->opts.use_graph && !timing) {
@@ -769,6 +804,8 @@ extern "C" crash_status crash_step_batch(crash_ctx* c, double dt, const uint64_t
     c->launches += nk;
   }
   c->step_host += 1;
+  c->chem_pending = !c->opts.chemistry;
+  c->last_dt = dt;
   return CRASH_OK;
 }
 
@@ -870,6 +907,65 @@ extern "C" crash_status crash_write_fields(crash_ctx* c, int f, const void* in) 
   return crash_write_fields_box(c, 0, f, in);
 }
 
+// ---------------------------------------------------------------- exchange
+extern "C" crash_status crash_deposits_device(crash_ctx* c, int box, void** dev_ptr, int64_t* n_cells) {
+  if (!c) return CRASH_ERR_ARG;
+  if (!dev_ptr) return set_err(c, CRASH_ERR_ARG, "dev_ptr is NULL");
+  if (box < 0 || box >= c->n_boxes) return set_err(c, CRASH_ERR_ARG, "box index out of range");
+  *dev_ptr = (void*)(c->dep + 4 * c->meta[box].cell_off);
+  if (n_cells) *n_cells = c->meta[box].ncell;
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_read_deposits(crash_ctx* c, int box, int64_t* out) {
+  if (!c) return CRASH_ERR_ARG;
+  if (!out) return set_err(c, CRASH_ERR_ARG, "output is NULL");
+  if (box < 0 || box >= c->n_boxes) return set_err(c, CRASH_ERR_ARG, "box index out of range");
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  crash_status st = check_device_error(c);
+  if (st != CRASH_OK) return st;
+  const BoxMeta& m = c->meta[box];
+  CK(cudaMemcpy(out, c->dep + 4 * m.cell_off, (size_t)m.ncell * 32, cudaMemcpyDeviceToHost));
+  return CRASH_OK;
+}
+
+extern "C" crash_status crash_write_deposits(crash_ctx* c, int box, const int64_t* in) {
+  if (!c) return CRASH_ERR_ARG;
+  if (!in) return set_err(c, CRASH_ERR_ARG, "input is NULL");
+  if (box < 0 || box >= c->n_boxes) return set_err(c, CRASH_ERR_ARG, "box index out of range");
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  const BoxMeta& m = c->meta[box];
+  CK(cudaMemcpy(c->dep + 4 * m.cell_off, in, (size_t)m.ncell * 32, cudaMemcpyHostToDevice));
+  return CRASH_OK;
+}
+
+// the chemistry's sub-step count of a separate per-cell update joins the totals
+__global__ void k_add_substeps(const unsigned long long* budget, unsigned long long* totals, int n) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n) totals[8 * b + 7] += budget[8 * b + 7];
+}
+
+extern "C" crash_status crash_chemistry(crash_ctx* c, double dt) {
+  if (!c) return CRASH_ERR_ARG;
+  if (!c->chem_pending)
+    return set_err(c, CRASH_ERR_STATE, "crash_chemistry follows one step run with chemistry = 0");
+  if (!(dt == c->last_dt)) return set_err(c, CRASH_ERR_ARG, "crash_chemistry needs the dt of its step");
+  cudaSetDevice(c->device);
+  StepArgs a = make_args(c, dt, 0);
+  a.chemistry = 1;
+  {
+    NvtxRange chem_range("chemistry");
+    launch_chemistry(a, c->stream);
+  }
+  k_add_substeps<<<(c->n_boxes + 127) / 128, 128, 0, c->stream>>>(c->budget, c->totals, c->n_boxes);
+  CK(cudaGetLastError());
+  c->launches += 2;
+  c->chem_pending = false;
+  return CRASH_OK;
+}
+
 // ---------------------------------------------------------------- timing
 extern "C" crash_status crash_kernel_time(crash_ctx* c, double* ms, int64_t* launches) {
   if (!c || !ms || !launches) return set_err(c, CRASH_ERR_ARG, "NULL argument");
@@ -954,16 +1050,19 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
       for (int sg : segs)
         for (int rs : resorts) trials.push_back({bs, sg, rs, cap, 0});
   if (c->precision == CRASH_MIXED) trials.push_back({256, 0, 1, 0, 1});
-  // the fastest configuration is then tried once more with Hilbert-ordered
-  // bucket keys (trial index -1)
-  for (int ti = 0; ti <= (int)trials.size(); ++ti) {
-    const bool curve_trial = ti == (int)trials.size();
-    if (curve_trial && (c->precision != CRASH_MIXED || best.tile || best_ms >= 1e300)) break;
-    const Trial tr = curve_trial ? Trial{best.block_size, best.seg_per_iter, best.resort_interval,
-                                         best.reg_cap, best.tile}
-                                 : trials[ti];
+  // the grid of trials runs one launch per pass; the fastest configuration is
+  // then tried once more with Hilbert-ordered bucket keys, and the fastest of
+  // those once more as one persistent launch per step
+  const int n_grid = (int)trials.size();
+  for (int ti = 0; ti < n_grid + 2; ++ti) {
+    const bool curve_trial = ti == n_grid, pers_trial = ti == n_grid + 1;
+    if ((curve_trial || pers_trial) && (c->precision != CRASH_MIXED || best.tile || best_ms >= 1e300)) break;
+    const Trial tr = ti >= n_grid ? Trial{best.block_size, best.seg_per_iter, best.resort_interval,
+                                          best.reg_cap, best.tile}
+                                  : trials[ti];
     crash_run_opts o = base;
-    o.sort_curve = curve_trial ? 1 : 0;
+    o.sort_curve = curve_trial ? 1 : (pers_trial ? best.sort_curve : 0);
+    o.persistent = pers_trial ? 1 : 0;
     o.block_size = tr.bs;
     o.seg_per_iter = tr.sg;
     o.resort_interval = tr.rs;
@@ -999,6 +1098,7 @@ extern "C" crash_status crash_autotune(crash_ctx* c, double dt, const uint64_t* 
       best.reg_cap = tr.cap;
       best.tile = tr.tile;
       best.sort_curve = o.sort_curve;
+      best.persistent = o.persistent;
     }
   }
   c->opts = best;

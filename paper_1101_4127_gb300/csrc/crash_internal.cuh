@@ -34,7 +34,7 @@ struct BoxMeta {
   int src_off;         // sources [src_off, src_off + n_src)
   int n_src;
   int heatF;           // heat unit 2^heatF eV (per photon quantum)
-  double ndot_max;     // max photon rate over the box's sources
+  double ndot_sum;     // photon rate of all the box's sources, summed in source order
   // per-step packet plan
   uint64_t pkts_per_src;   // N_s = packets_per_step / n_src
   uint32_t win_lo, win_hi; // traced packet ids [win_lo, win_hi) per source
@@ -48,9 +48,16 @@ struct BoxMeta {
   // morton(ix >> 4, iy >> 4, iz >> 4) (tile_bits bits per axis) * 8 + octant
   int64_t tile_off;
   int tile_bits;
-  int max_iter;            // nx + ny + nz + 3: bound on DDA steps of one packet
+  int max_iter;            // bound on the DDA steps of one packet: nx + ny + nz + 3, or
+                           // 2 L + 4 in a periodic box whose packets travel L cells
   double f_rec;            // > 0: diffuse recombination field with this re-emission threshold
+  int coupling;            // 1: photon-conserving transport -> chemistry coupling
+  int periodic;            // 1: periodic box, walks end after c dt
+  float path_cells32;      // periodic: c dt / dl of this step in FP32 (mixed form)
 };
+
+// speed of light (cm/s): the periodic box's light-travel distance per step
+#define CRASH_C_LIGHT 2.99792458e10
 
 // Cross sections and heating weights per species and bin (passed by value;
 // kernel parameters live in the constant bank).
@@ -95,6 +102,8 @@ struct StepArgs {
   // options
   int any_he;                // some box has helium (selects the H+He kernels)
   int any_heat;              // some box evolves T (selects the heating deposit)
+  int any_periodic;          // some box is periodic (selects the wrapping walks)
+  int max_iter_step;         // largest per-box DDA bound of this step
   int chemistry;
   int fp32_rates;            // mixed form: rate fits evaluated in FP32
   double chem_eps;

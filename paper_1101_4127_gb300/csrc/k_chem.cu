@@ -9,11 +9,16 @@
 // network is sub-sampled when the step exceeds its time-scales.
 //
 // Coupling of transport to chemistry (step-synchronous form): the step's
-// deposit of species s, dep_s quanta of 2^E photons, defines a
-// photo-ionisation rate per absorber Gamma_s = dep_s 2^E / (dt n_s^0 V) with
-// n_s^0 the absorber density frozen at the start of the step; photo-heating
-// is the mean excess energy per absorbed photon times the photo-ionisation
-// rate of the current absorbers.
+// deposit of species s, dep_s quanta of 2^E photons, defines either
+//   * (coupling 0) a photo-ionisation rate per absorber
+//     Gamma_s = dep_s 2^E / (dt n_s^0 V) with n_s^0 the absorber density
+//     frozen at the start of the step; photo-heating is the mean excess
+//     energy per absorbed photon times the photo-ionisation rate of the
+//     current absorbers; or
+//   * (coupling 1, photon-conserving) a constant source of dep_s 2^E / (dt V)
+//     ionisations per cm^3 and s, in each sub-step at most the atoms of the
+//     species present (the photons beyond are lost); photo-heating at the
+//     constant deposited rate.
 //
 // Integrator per sub-step h (h limited so that no ionic fraction changes by
 // more than eps * max(x, 1e-3) and T by more than eps * T; the last allowed
@@ -115,6 +120,7 @@ __device__ __forceinline__ double cooling_rate(const Rates& r, int mask, double 
 
 struct CellIn {
   double nH, nHe, GH, G1, G2, eps_heat, Tcmb, ccomp, eps, V;
+  double SH, S1, S2, heat_rate;   // constant sources per atom of the element (s^-1), erg/cm^3/s
   int iso, caseB, mask, max_sub, count_rec;
 };
 
@@ -147,9 +153,14 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   // rates of change at the start of the sub-step (for the step size)
   const double IH = c.GH + bH * ne, RH = aH * ne;
   const double I1 = c.G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = c.G2 + bHe2 * ne, R3 = aHe3 * ne;
-  const double dx = IH * (1.0 - x) - RH * x;
-  const double dy1 = -I1 * y1 + R2 * y2;
-  const double dy3 = I2 * y2 - R3 * y3;
+  // constant sources (photon-conserving coupling), for the step size at most
+  // what the atoms present can take over the time left
+  double sH = fmin(c.SH, (1.0 - x) / rem);
+  double s1 = fmin(c.S1, y1 / rem);
+  double s2 = fmin(c.S2, y2 / rem);
+  const double dx = (sH + IH * (1.0 - x)) - RH * x;
+  const double dy1 = (-I1 * y1 + R2 * y2) - s1;
+  const double dy3 = (s2 + I2 * y2) - R3 * y3;
   const double dy2 = -dy1 - dy3;
   double h = rem;
   {
@@ -165,7 +176,7 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double ntot = c.nH + c.nHe + ne;
   if (!c.iso) {
     const double nHI = c.nH * (1.0 - x), nHII = c.nH * x;
-    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2);
+    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2) + c.heat_rate;
     const double L = cooling_rate(r, c.mask, ne, nHI, nHII, c.nHe * y1, c.nHe * y2, c.nHe * y3) +
                      c.ccomp * ne * (T - c.Tcmb);
     const double dne = c.nH * dx + c.nHe * (dy2 + 2.0 * dy3);
@@ -174,12 +185,17 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
     if (adT * h > c.eps * T) h = c.eps * T / adT;
   }
   if (nsub == c.max_sub - 1 || !(h < rem)) h = rem;
+  // the sources of the sub-step ionise at most the atoms present (He II also
+  // what He I gives it): the photons beyond are lost
+  sH = fmin(c.SH, (1.0 - x) / h);
+  s1 = fmin(c.S1, y1 / h);
+  s2 = fmin(c.S2, y2 / h + s1);
   // implicit ionisation update
   double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
 #pragma unroll 1
   for (int it = 0; it < 4; ++it) {
     const double ih = c.GH + bH * nen, rh = aH * nen;
-    xn = (x + h * ih) / (1.0 + h * (ih + rh));
+    xn = (x + h * (sH + ih)) / (1.0 + h * (ih + rh));
     if (he) {
       const double i1 = c.G1 + bHe1 * nen, r2 = aHe2 * nen;
       const double i2 = c.G2 + bHe2 * nen, r3 = aHe3 * nen;
@@ -187,11 +203,13 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
       const double a11 = 1.0 + h * i1, a12 = -h * r2;
       const double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
       const double a32 = -h * i2, a33 = 1.0 + h * r3;
+      // right-hand side: the old fractions plus the constant sources
+      const double b1 = y1 - h * s1, b2 = y2 + h * (s1 - s2), b3 = y3 + h * s2;
       const double inv11 = 1.0 / a11;
-      const double c1 = a12 * inv11, d1 = y1 * inv11;
+      const double c1 = a12 * inv11, d1 = b1 * inv11;
       const double inv2 = 1.0 / (a22 - a21 * c1);
-      const double c2 = a23 * inv2, d2 = (y2 - a21 * d1) * inv2;
-      y3n = (y3 - a32 * d2) / (a33 - a32 * c2);
+      const double c2 = a23 * inv2, d2 = (b2 - a21 * d1) * inv2;
+      y3n = (b3 - a32 * d2) / (a33 - a32 * c2);
       y2n = d2 - c2 * y3n;
       y1n = d1 - c1 * y2n;
     }
@@ -213,7 +231,7 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double ne2 = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
   if (!c.iso) {
     const double nHI = c.nH * (1.0 - xn), nHII = c.nH * xn;
-    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n);
+    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n) + c.heat_rate;
     const double L = cooling_rate(r, c.mask, ne2, nHI, nHII, c.nHe * y1n, c.nHe * y2n,
                                   c.nHe * y3n);
     const double L1 = L / T;
@@ -256,11 +274,24 @@ __device__ __forceinline__ void load_cell(const StepArgs& a, int64_t i, int b, C
   const ulonglong2 d23 = reinterpret_cast<const ulonglong2*>(a.dep)[2 * i + 1];
   const long long dHI = (long long)d01.x, dHeI = (long long)d01.y;
   const long long dHeII = (long long)d23.x, dE = (long long)d23.y;
-  c.GH = NHI > 0 ? ((double)dHI * q) / (a.dt * NHI) : 0.0;
-  c.G1 = NHeI > 0 ? ((double)dHeI * q) / (a.dt * NHeI) : 0.0;
-  c.G2 = NHeII > 0 ? ((double)dHeII * q) / (a.dt * NHeII) : 0.0;
-  const long long nabs = (dHI + dHeI) + dHeII;
-  c.eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
+  c.SH = c.S1 = c.S2 = c.heat_rate = 0.0;
+  if (!M->coupling) {
+    c.GH = NHI > 0 ? ((double)dHI * q) / (a.dt * NHI) : 0.0;
+    c.G1 = NHeI > 0 ? ((double)dHeI * q) / (a.dt * NHeI) : 0.0;
+    c.G2 = NHeII > 0 ? ((double)dHeII * q) / (a.dt * NHeII) : 0.0;
+    const long long nabs = (dHI + dHeI) + dHeII;
+    c.eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
+  } else {
+    // photon-conserving: one ionisation per absorbed photon at a constant
+    // rate per atom of the element, heating at the deposited rate
+    const double NH = c.nH * V, NHe = c.nHe * V;
+    c.GH = c.G1 = c.G2 = 0.0;
+    c.eps_heat = 0.0;
+    c.SH = NH > 0 ? ((double)dHI * q) / (a.dt * NH) : 0.0;
+    c.S1 = NHe > 0 ? ((double)dHeI * q) / (a.dt * NHe) : 0.0;
+    c.S2 = NHe > 0 ? ((double)dHeII * q) / (a.dt * NHe) : 0.0;
+    c.heat_rate = ((double)dE * qE) / (a.dt * V);
+  }
   c.iso = M->isothermal;
   // the diffuse recombination field replaces on-the-spot absorption: case A
   c.caseB = M->f_rec > 0.0 ? 0 : M->caseB;

@@ -73,8 +73,9 @@ __global__ void k_budget(StepArgs a, int n_bins) {
   if (s >= a.n_src_total) return;
   int b = box_of_source(a.boxes, a.n_boxes, s);
   const BoxMeta& M = a.boxes[b];
-  // quantum q = 2^E with n_src * max(ndot) * dt / q <= 2^62
-  double X = ((double)M.n_src * M.ndot_max) * a.dt;
+  // quantum q = 2^E with the step's photons of all the box's sources,
+  // (sum of ndot) dt / q, at most 2^62
+  double X = M.ndot_sum * a.dt;
   int E = X > 0.0 ? ceil_log2_dev(X) - 62 : 0;
   // the diffuse recombination field re-emits this step at most ncell times
   // the largest count over its threshold: the quantum also keeps that below
@@ -158,6 +159,9 @@ __device__ __forceinline__ void flush_tally(const StepArgs& a, int b, Tally t) {
 // 1987, ties x before y before z): per crossed cell with path l > 0, per bin
 // Eq. 1 in integer quanta N' = rint(N e^-tau), the absorbed A = N - N' split
 // by optical-depth share (Sec. 2), excess energy rounded once per cell.
+// In a periodic box (Sec. 2) the walk re-enters through the opposite face and
+// ends after the light-travel distance c dt (the last segment cut there),
+// what the packet still holds then being counted as escaped.
 // Deposits go to the grid, counts to tl; the content N is consumed.
 template <int NBT, bool HE, bool HEAT>
 __device__ __forceinline__ void walk_fp64(const StepArgs& a, const BinTables& t, const BoxMeta* M,
@@ -181,13 +185,18 @@ __device__ __forceinline__ void walk_fp64(const StepArgs& a, const BinTables& t,
   bool escaped = (ix < 0 || ix >= nx || iy < 0 || iy >= ny || iz < 0 || iz >= nz);
   bool done = escaped;
   double tcur = 0.0;
-  const int max_iter = nx + ny + nz + 3;
-  int it = 0;
+  // a path of length L crosses at most (|dx| + |dy| + |dz|) L + 3 < 2 L + 3 faces
+  const bool per = M->periodic != 0;
+  const double tlim = per ? (CRASH_C_LIGHT * a.dt) / dl : INFINITY;
+  const int64_t max_iter = per ? (int64_t)(2.0 * tlim) + 4 : (int64_t)(nx + ny + nz + 3);
+  int64_t it = 0;
   for (; !done && it < max_iter; ++it) {
     int ax = 0;
     double tn = tMx;
     if (tMy < tn) { ax = 1; tn = tMy; }
     if (tMz < tn) { ax = 2; tn = tMz; }
+    const bool stop = tn >= tlim;
+    if (stop) tn = tlim;
     const double seg = tn - tcur;
     if (seg > 0) {
       const int64_t cell = coff + (int64_t)ix + (int64_t)nx * ((int64_t)iy + (int64_t)ny * iz);
@@ -253,10 +262,18 @@ __device__ __forceinline__ void walk_fp64(const StepArgs& a, const BinTables& t,
       tl.crossings += 1;
       if (left == 0) { done = true; break; }
     }
+    if (stop) { escaped = true; done = true; break; }
     tcur = tn;
-    if (ax == 0) { tMx += tDx; ix += sx; escaped = (ix < 0 || ix >= nx); }
-    else if (ax == 1) { tMy += tDy; iy += sy; escaped = (iy < 0 || iy >= ny); }
-    else { tMz += tDz; iz += sz; escaped = (iz < 0 || iz >= nz); }
+    if (ax == 0) { tMx += tDx; ix += sx; }
+    else if (ax == 1) { tMy += tDy; iy += sy; }
+    else { tMz += tDz; iz += sz; }
+    if (per) {
+      ix = ix < 0 ? nx - 1 : (ix >= nx ? 0 : ix);
+      iy = iy < 0 ? ny - 1 : (iy >= ny ? 0 : iy);
+      iz = iz < 0 ? nz - 1 : (iz >= nz ? 0 : iz);
+    } else {
+      escaped = (ix < 0 || ix >= nx || iy < 0 || iy >= ny || iz < 0 || iz >= nz);
+    }
     if (escaped) done = true;
   }
   if (escaped) {

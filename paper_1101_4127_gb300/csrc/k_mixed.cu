@@ -45,6 +45,7 @@ struct WF {
   unsigned* boff = nullptr;              // [n_keys]
   unsigned* bsum = nullptr;              // [1024]
   uint2* items = nullptr;                // work items of a tile pass (tile, first position)
+  unsigned* gsync = nullptr;             // [2] grid barrier of the persistent launch
   int64_t n_keys = 0;
 };
 
@@ -487,13 +488,18 @@ struct TileCells {
 // requested before the current cell's bins are processed (one step of
 // software pipelining hides most of the gather latency).  With TILE the walk
 // also stops (alive) when it steps out of the box [tx0,tx0+ex) x ... .
-template <int NBT, bool HE, bool HEAT, bool TILE, class Cells>
+// With PER, a box flagged periodic wraps the walk at its faces and ends it
+// (ESCAPED) once the path trem (cells, the rest of c dt) is used up, the
+// last segment cut there (Sec. 2 periodic boxes).
+template <int NBT, bool HE, bool HEAT, bool TILE, bool PER, class Cells>
 __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float& tMy, float& tMz,
                                     const float dx, const float dy, const float dz, Content<NBT>& N,
                                     const BoxMeta* M, const Cells& cells, const BinTables& t,
                                     const int nb, const int max_iter, Tally& tl, int tx0 = 0,
-                                    int ty0 = 0, int tz0 = 0, int ex = 0, int ey = 0, int ez = 0) {
+                                    int ty0 = 0, int tz0 = 0, int ex = 0, int ey = 0, int ez = 0,
+                                    float* trem = nullptr) {
   const int nx = M->nx, ny = M->ny, nz = M->nz;
+  const bool per = PER && M->periodic;
   const float tDx = dx != 0.f ? 1.0f / fabsf(dx) : INFINITY;
   const float tDy = dy != 0.f ? 1.0f / fabsf(dy) : INFINITY;
   const float tDz = dz != 0.f ? 1.0f / fabsf(dz) : INFINITY;
@@ -515,6 +521,11 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
     ix += bx ? sx : 0;
     iy += by ? sy : 0;
     iz += bz ? sz : 0;
+    if (PER && per) {
+      ix = ix < 0 ? nx - 1 : (ix >= nx ? 0 : ix);
+      iy = iy < 0 ? ny - 1 : (iy >= ny ? 0 : iy);
+      iz = iz < 0 ? nz - 1 : (iz >= nz ? 0 : iz);
+    }
     const bool out = ((unsigned)ix >= (unsigned)nx) | ((unsigned)iy >= (unsigned)ny) |
                      ((unsigned)iz >= (unsigned)nz);
     const bool leave = TILE ? (((unsigned)(ix - tx0) >= (unsigned)ex) | ((unsigned)(iy - ty0) >= (unsigned)ey) |
@@ -530,6 +541,13 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
       cell_n = cells.index(ix, iy, iz);
       ab_n = cells.load(cell_n, ix, iy, iz);
     }
+    // periodic: the path left to the light-travel distance cuts the segment
+    bool stop = false;
+    if (PER && per) {
+      stop = seg >= *trem;
+      if (stop) seg = *trem;
+      *trem -= seg;
+    }
     // attenuate and deposit in the current cell
     if (seg > 0.f) {
       long long dHI, dHeI, dHeII, dE;
@@ -543,6 +561,7 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
       tl.crossings += 1;
       if (left == 0) return ABSORBED;
     }
+    if (PER && stop) return ESCAPED;
     if (out) return ESCAPED;
     if (TILE && leave) return ALIVE;
     if (it >= max_iter) return ALIVE;
@@ -554,18 +573,18 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
 }
 
 // the walk over the grid in global memory
-template <int NBT, bool HE, bool HEAT>
+template <int NBT, bool HE, bool HEAT, bool PER = false>
 __device__ __forceinline__ int trace_mixed(int& ix, int& iy, int& iz, float& tMx, float& tMy,
                                            float& tMz, const float dx, const float dy,
                                            const float dz, Content<NBT>& N, const BoxMeta* M,
                                            const StepArgs& a, const BinTables& t, const int nb,
-                                           const int max_iter, Tally& tl) {
+                                           const int max_iter, Tally& tl, float* trem = nullptr) {
   __shared__ __align__(16) unsigned long long stage[kStageThreads * 8];
   const bool bulk = threadIdx.x < kStageThreads && ((uintptr_t)a.dep & 15u) == 0;
   GlobalCells cells{reinterpret_cast<const float4*>(a.abs32), a.dep, M->cell_off, M->nx, M->ny,
                     bulk ? stage + 8 * threadIdx.x : nullptr, 0};
-  const int r = walk<NBT, HE, HEAT, false>(ix, iy, iz, tMx, tMy, tMz, dx, dy, dz, N, M, cells, t, nb,
-                                           max_iter, tl);
+  const int r = walk<NBT, HE, HEAT, false, PER>(ix, iy, iz, tMx, tMy, tMz, dx, dy, dz, N, M, cells, t,
+                                                nb, max_iter, tl, 0, 0, 0, 0, 0, 0, trem);
   if (bulk) bulk_wait_all();
   return r;
 }
@@ -629,8 +648,8 @@ __device__ __forceinline__ void load_record(const char* rec, int rs, long long i
                                             int& iz, int& box, float& tMx, float& tMy, float& tMz,
                                             float& dx, float& dy, float& dz, Content<NBT>& c, int nb) {
   const char* r = rec + (int64_t)rs * i;
-  const float4 td = *reinterpret_cast<const float4*>(r);
-  const uint4 cd = *reinterpret_cast<const uint4*>(r + 16);
+  const float4 td = __ldcg(reinterpret_cast<const float4*>(r));
+  const uint4 cd = __ldcg(reinterpret_cast<const uint4*>(r + 16));
   tMx = td.x; tMy = td.y; tMz = td.z; dx = td.w;
   ix = (int)(cd.x & 0xFFFFu); iy = (int)(cd.x >> 16);
   iz = (int)(cd.y & 0xFFFFu); box = (int)((cd.y >> 16) & 0x7FFu);
@@ -641,7 +660,7 @@ __device__ __forceinline__ void load_record(const char* rec, int rs, long long i
 #pragma unroll
   for (int j = 0; j < (NBT > 0 ? (NBT + 3) / 4 : CRASH_MAX_BINS / 4); ++j) {
     if (NBT == 0 && 4 * j >= nb) break;
-    const uint4 v = m4[j];
+    const uint4 v = __ldcg(m4 + j);
     const int k = 4 * j;
     c.m[k] = v.x;
     if (k + 1 < lim) c.m[k + 1] = v.y;
@@ -654,38 +673,51 @@ __device__ __forceinline__ void load_record(const char* rec, int rs, long long i
 // pass reads in sorted order) the record's key and its rank among the
 // records of that key (one atomic per group of equal keys in the warp).
 template <int NBT>
-__device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& w, bool alive, int ix,
-                                               int iy, int iz, int box, float tMx, float tMy, float tMz,
-                                               float dx, float dy, float dz, const Content<NBT>& N,
-                                               int nb) {
-  const long long slot = append_slot(alive, w.count_out);
+__device__ __forceinline__ void write_survivor_to(const StepArgs& a, unsigned* count_out, int64_t cap, char* rec_out,
+                                                  int rs, bool write_keys, unsigned* key, unsigned* rank,
+                                                  unsigned* bcount, int tile, int curve, bool alive, int ix,
+                                                  int iy, int iz, int box, float tMx, float tMy, float tMz,
+                                                  float dx, float dy, float dz, const Content<NBT>& N, int nb) {
+  const long long slot = append_slot(alive, count_out);
   bool ok = alive;
-  if (alive && slot >= w.cap) {
+  if (alive && slot >= cap) {
     atomicOr(a.err, ERR_QUEUE);
     ok = false;
   }
-  if (ok) store_record<NBT>(w.rec_out, w.rs, slot, ix, iy, iz, box, tMx, tMy, tMz, dx, dy, dz, N, nb);
-  if (w.key) {
-    const unsigned k = ok ? sort_key(a.boxes, box, ix, iy, iz, dx, dy, dz, w.tile, w.curve) : 0xFFFFFFFFu;
+  if (ok) store_record<NBT>(rec_out, rs, slot, ix, iy, iz, box, tMx, tMy, tMz, dx, dy, dz, N, nb);
+  if (write_keys) {
+    const unsigned k = ok ? sort_key(a.boxes, box, ix, iy, iz, dx, dy, dz, tile, curve) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
     if (ok) {
       const int lane = threadIdx.x & 31;
       const int leader = __ffs(peers) - 1;
       unsigned r0 = 0;
-      if (lane == leader) r0 = atomicAdd(&w.bcount[k], (unsigned)__popc(peers));
+      if (lane == leader) r0 = atomicAdd(&bcount[k], (unsigned)__popc(peers));
       r0 = __shfl_sync(peers, r0, leader);
-      w.key[slot] = k;
-      w.rank[slot] = r0 + __popc(peers & ((1u << lane) - 1u));
+      key[slot] = k;
+      rank[slot] = r0 + __popc(peers & ((1u << lane) - 1u));
     }
   }
+}
+
+template <int NBT>
+__device__ __forceinline__ void write_survivor(const StepArgs& a, const WFArgs& w, bool alive, int ix,
+                                               int iy, int iz, int box, float tMx, float tMy, float tMz,
+                                               float dx, float dy, float dz, const Content<NBT>& N,
+                                               int nb) {
+  write_survivor_to<NBT>(a, w.count_out, w.cap, w.rec_out, w.rs, w.key != nullptr, w.key, w.rank, w.bcount,
+                         w.tile, w.curve, alive, ix, iy, iz, box, tMx, tMy, tMz, dx, dy, dz, N, nb);
 }
 
 // ------------------------------------------------------------------ emission
 // MINB = 3 keeps three 256-thread blocks resident per SM (at most 85
 // registers); MINB = 4 caps the kernels at 64 registers for four.
-template <int NBT, bool HE, bool HEAT, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables t, WFArgs w, int64_t g0,
-                                                   int64_t n, int S, int max_steps_all) {
+// Emission of the packets [g0, g0 + n) of the launch, grid-stride over the
+// calling grid: each is traced S steps (0: emission only) and, when the launch
+// keeps a queue (S < max_steps_all), written to it with its sort key.
+template <int NBT, bool HE, bool HEAT, bool PER>
+__device__ __forceinline__ void emit_range(const StepArgs& a, const BinTables& t, const WFArgs& w, int64_t g0,
+                                           int64_t n, int S, int max_steps_all) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const uint32_t step = (uint32_t)*a.step_dev;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -732,10 +764,13 @@ __global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables 
         tMx = fx > 0.f ? ((float)(ix + 1) - px) / fx : (fx < 0.f ? ((float)ix - px) / fx : INFINITY);
         tMy = fy > 0.f ? ((float)(iy + 1) - py) / fy : (fy < 0.f ? ((float)iy - py) / fy : INFINITY);
         tMz = fz > 0.f ? ((float)(iz + 1) - pz) / fz : (fz < 0.f ? ((float)iz - pz) / fz : INFINITY);
-        const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
-                                                 nb, S, tl);
+        float trem = PER ? M->path_cells32 : 0.f;
+        const int r = trace_mixed<NBT, HE, HEAT, PER>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
+                                                      nb, S, tl, &trem);
         if (r == ESCAPED) tl.escaped += N.total(nb);
         alive = (r == ALIVE);
+        // traced to the end (no queue to keep it): a packet still alive hit the DDA bound
+        if (alive && S >= max_steps_all) atomicOr(a.err, ERR_DDA_LIMIT);
       }
     }
     if (S < max_steps_all)   // a wavefront launch: keep the survivors
@@ -744,12 +779,18 @@ __global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables 
   }
 }
 
+template <int NBT, bool HE, bool HEAT, int MINB, bool PER = false>
+__global__ void __launch_bounds__(256, MINB) k_emit_mixed(StepArgs a, BinTables t, WFArgs w, int64_t g0,
+                                                   int64_t n, int S, int max_steps_all) {
+  emit_range<NBT, HE, HEAT, PER>(a, t, w, g0, n, S, max_steps_all);
+}
+
 // One re-emission packet per entry of this step's list (diffuse
 // recombination field), traced to the end by its own thread: start point
 // and direction from the cell's Philox counters, the photons of each species
 // in its bin held as 32-bit counts of 2^e quanta as for a source packet.
 // Entries are read in any order: deposits and counts do not depend on it.
-template <int NBT, bool HE, bool HEAT>
+template <int NBT, bool HE, bool HEAT, bool PER>
 __global__ void __launch_bounds__(256, 3) k_rec_mixed(StepArgs a, BinTables t) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const int64_t n = (int64_t)*a.rec_count;
@@ -789,8 +830,9 @@ __global__ void __launch_bounds__(256, 3) k_rec_mixed(StepArgs a, BinTables t) {
         float tMx = fx > 0.f ? ((float)(ix + 1) - px) / fx : (fx < 0.f ? ((float)ix - px) / fx : INFINITY);
         float tMy = fy > 0.f ? ((float)(iy + 1) - py) / fy : (fy < 0.f ? ((float)iy - py) / fy : INFINITY);
         float tMz = fz > 0.f ? ((float)(iz + 1) - pz) / fz : (fz < 0.f ? ((float)iz - pz) / fz : INFINITY);
-        const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
-                                                 nb, M->max_iter, tl);
+        float trem = PER ? M->path_cells32 : 0.f;
+        const int r = trace_mixed<NBT, HE, HEAT, PER>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
+                                                      nb, M->max_iter, tl, &trem);
         if (r == ESCAPED) tl.escaped += N.total(nb);
         else if (r == ALIVE) atomicOr(a.err, ERR_DDA_LIMIT);
       }
@@ -803,14 +845,19 @@ int num_sms();
 
 template <int NBT, bool HE, bool HEAT>
 void launch_rec_t(const StepArgs& a, const BinTables& t, cudaStream_t s) {
-  k_rec_mixed<NBT, HE, HEAT><<<(unsigned)(num_sms() * 3), 256, 0, s>>>(a, t);
+  if (a.any_periodic) k_rec_mixed<NBT, HE, HEAT, true><<<(unsigned)(num_sms() * 3), 256, 0, s>>>(a, t);
+  else k_rec_mixed<NBT, HE, HEAT, false><<<(unsigned)(num_sms() * 3), 256, 0, s>>>(a, t);
 }
 
 // ------------------------------------------------------------------ passes
-template <int NBT, bool HE, bool HEAT, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_pass_mixed(StepArgs a, BinTables t, WFArgs w, int S) {
+// One pass over the queue w.count_in holds, grid-stride over the calling
+// grid: every packet advances at most S cells; survivors go to the output
+// queue.  The queue is read through L2 (ld.global.cg): in the persistent
+// launch other blocks of the same grid wrote it.
+template <int NBT, bool HE, bool HEAT>
+__device__ __forceinline__ void pass_range(const StepArgs& a, const BinTables& t, const WFArgs& w, int S) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
-  const int64_t n = (int64_t)*w.count_in;
+  const int64_t n = (int64_t)__ldcg(w.count_in);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   Tally tl{0, 0, 0, 0u, 0u};
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -822,7 +869,7 @@ __global__ void __launch_bounds__(256, MINB) k_pass_mixed(StepArgs a, BinTables 
     Content<NBT> N;
     N.e = 0;
     if (j < n) {
-      const int64_t i = w.perm ? (int64_t)w.perm[j] : j;
+      const int64_t i = w.perm ? (int64_t)__ldcg(w.perm + j) : j;
       load_record<NBT>(w.rec_in, w.rs, i, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
       const BoxMeta* M = a.boxes + b;
       const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
@@ -831,6 +878,44 @@ __global__ void __launch_bounds__(256, MINB) k_pass_mixed(StepArgs a, BinTables 
       alive = (r == ALIVE);
     }
     write_survivor<NBT>(a, w, alive, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
+    flush_warp(a, b, tl);
+  }
+}
+
+template <int NBT, bool HE, bool HEAT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pass_mixed(StepArgs a, BinTables t, WFArgs w, int S) {
+  pass_range<NBT, HE, HEAT>(a, t, w, S);
+}
+
+// The same pass for the persistent launch, the input queue CUR (0 or 1)
+// fixed at compile time: its pointers are read from the kernel's parameter
+// bank as in the one-launch-per-pass kernel instead of occupying registers.
+template <int NBT, bool HE, bool HEAT, int CUR>
+__device__ __forceinline__ void pass_range_q(const StepArgs& a, const BinTables& t, const WF& wf, int S,
+                                             bool read_sorted, bool write_keys, int curve) {
+  const int nb = NBT > 0 ? NBT : t.n_bins;
+  const int64_t n = (int64_t)__ldcg(wf.count + CUR);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  Tally tl{0, 0, 0, 0u, 0u};
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t j = base + threadIdx.x;
+    int b = -1;
+    bool alive = false;
+    int ix = 0, iy = 0, iz = 0;
+    float tMx = 0.f, tMy = 0.f, tMz = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    Content<NBT> N;
+    N.e = 0;
+    if (j < n) {
+      const int64_t i = read_sorted ? (int64_t)__ldcg(wf.perm + j) : j;
+      load_record<NBT>(wf.rec[CUR], wf.rs, i, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
+      const BoxMeta* M = a.boxes + b;
+      const int r = trace_mixed<NBT, HE, HEAT>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, a, t,
+                                               nb, S, tl);
+      if (r == ESCAPED) tl.escaped += N.total(nb);
+      alive = (r == ALIVE);
+    }
+    write_survivor_to<NBT>(a, wf.count + (1 - CUR), wf.cap, wf.rec[1 - CUR], wf.rs, write_keys, wf.key, wf.rank,
+                           wf.bcount, 0, curve, alive, ix, iy, iz, b, tMx, tMy, tMz, fx, fy, fz, N, nb);
     flush_warp(a, b, tl);
   }
 }
@@ -1021,8 +1106,8 @@ __global__ void __launch_bounds__(kTileBlock, 1) k_tile_pass(StepArgs a, BinTabl
       if (j < hi) {
         load_record<NBT>(w.rec_in, w.rs, (long long)w.perm[j], ix, iy, iz, pb, tMx, tMy, tMz, fx, fy, fz,
                          N, nb);
-        const int r = walk<NBT, HE, HEAT, true>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells, t, nb,
-                                                64, tl, x0, y0, z0, ex, ey, ez);
+        const int r = walk<NBT, HE, HEAT, true, false>(ix, iy, iz, tMx, tMy, tMz, fx, fy, fz, N, M, cells,
+                                                       t, nb, 64, tl, x0, y0, z0, ex, ey, ez);
         if (r == ESCAPED) tl.escaped += N.total(nb);
         alive = (r == ALIVE);
       }
@@ -1050,22 +1135,185 @@ __global__ void k_check_drained(const unsigned* count, int* err) {
   if (*count != 0u) atomicOr(err, ERR_WATCHDOG);
 }
 
-WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys, int tile = 0, int curve = 0) {
+__host__ __device__ __forceinline__ WFArgs wf_args(const WF& wf, int in, bool read_sorted, bool write_keys,
+                                                    int tile = 0, int curve = 0) {
   WFArgs w;
   w.tile = tile;
   w.curve = curve;
   const int out = 1 - in;
-  w.rec_in = wf->rec[in];
-  w.rec_out = wf->rec[out];
-  w.count_in = wf->count + in;
-  w.count_out = wf->count + out;
-  w.perm = read_sorted ? wf->perm : nullptr;
-  w.key = write_keys ? wf->key : nullptr;
-  w.rank = write_keys ? wf->rank : nullptr;
-  w.bcount = wf->bcount;
-  w.rs = wf->rs;
-  w.cap = wf->cap;
+  w.rec_in = wf.rec[in];
+  w.rec_out = wf.rec[out];
+  w.count_in = wf.count + in;
+  w.count_out = wf.count + out;
+  w.perm = read_sorted ? wf.perm : nullptr;
+  w.key = write_keys ? wf.key : nullptr;
+  w.rank = write_keys ? wf.rank : nullptr;
+  w.bcount = wf.bcount;
+  w.rs = wf.rs;
+  w.cap = wf.cap;
   return w;
+}
+WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys, int tile = 0, int curve = 0) {
+  return wf_args(*wf, in, read_sorted, write_keys, tile, curve);
+}
+
+// ------------------------------------------------------------------ persistent
+// Grid barrier of a cooperative launch (every block resident at once): a
+// block arrives, then waits until the last one to arrive advances the
+// generation word.  Every wait is bounded by kBarrierLimitNs of %globaltimer
+// and ends early once any block has set the error word; false means the
+// launch stops (the host then reports the error word).
+constexpr unsigned long long kBarrierLimitNs = 30ull * 1000000000ull;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_sync(unsigned* gs, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = ld_acquire_u32(gs + 1);      // read before arriving
+    __threadfence();                                  // this block's writes, device-wide
+    if (atomicAdd(gs, 1u) == gridDim.x - 1) {
+      atomicExch(gs, 0u);
+      __threadfence();
+      atomicAdd(gs + 1, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_u32(gs + 1) == gen) {
+        if (*(volatile int*)err != 0) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+          atomicOr(err, ERR_WATCHDOG);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    s_ok = ok && *(volatile int*)err == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The whole wavefront transport of a step in one cooperative launch: chunk
+// after chunk of at most wf.cap packets, emission into queue 0, then the
+// passes, each reading the queue the previous one wrote; before a sorted pass
+// the counting sort runs in three phases between grid barriers (segment
+// scans of the key counts, the scan of the segment sums, the sorted position
+// boff[key] + bsum[key / 4096] + rank of every record).  The same device code
+// as the one-launch-per-pass sequence, so the deposits are the same bits.
+template <int NBT, bool HE, bool HEAT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_wavefront(StepArgs a, BinTables t, WF wf, int S, int R,
+                                                         int passes, int curve, int max_iter) {
+  __shared__ unsigned sh[32];
+  // the loop state lives in shared memory so that it holds no registers
+  // across the passes (the pass body needs every register of the cap)
+  __shared__ volatile long long s_g0;
+  __shared__ volatile int s_p, s_cur;
+  auto sorted_pass = [&](int p) { return p >= 1 && p < passes && R > 0 && (p % R) == 0; };
+  if (threadIdx.x == 0) s_g0 = 0;
+  __syncthreads();
+  while (s_g0 < a.total_packets) {
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g0 = s_g0;
+    const int64_t n = a.total_packets - g0 < wf.cap ? a.total_packets - g0 : wf.cap;
+    if (gtid == 0) {
+      wf.count[0] = 0u;
+      wf.count[1] = 0u;
+    }
+    if (sorted_pass(1))
+      for (int64_t k = gtid; k < wf.n_keys; k += gstride) wf.bcount[k] = 0u;
+    if (!grid_sync(wf.gsync, a.err)) return;
+    emit_range<NBT, HE, HEAT, false>(a, t, wf_args(wf, 1, false, sorted_pass(1), 0, curve), g0, n, 0,
+                                     max_iter);
+    if (!grid_sync(wf.gsync, a.err)) return;
+    if (threadIdx.x == 0) {
+      s_p = 1;
+      s_cur = 0;
+    }
+    __syncthreads();
+    while (s_p < passes) {
+      const int p = s_p, cur = s_cur;
+      const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+      const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+      const bool sorted_now = sorted_pass(p), keys_next = sorted_pass(p + 1);
+      if (sorted_now) {
+        const int64_t nk = wf.n_keys;
+        const int64_t nseg = (nk + 4095) / 4096;
+        for (int64_t seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+          const int64_t base = seg * 4096 + (int64_t)threadIdx.x * 16;
+          unsigned v[16], sum = 0u;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            v[k] = base + k < nk ? __ldcg(wf.bcount + base + k) : 0u;
+            sum += v[k];
+          }
+          unsigned tot;
+          unsigned ex = block_excl_scan(sum, sh, &tot);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            if (base + k < nk) wf.boff[base + k] = ex;
+            ex += v[k];
+          }
+          if (threadIdx.x == 0) wf.bsum[seg] = tot;
+        }
+        if (!grid_sync(wf.gsync, a.err)) return;
+        if (blockIdx.x == 0) {
+          unsigned v[4], sum = 0u;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int64_t idx = (int64_t)threadIdx.x * 4 + k;
+            v[k] = idx < nseg ? __ldcg(wf.bsum + idx) : 0u;
+            sum += v[k];
+          }
+          unsigned tot;
+          unsigned ex = block_excl_scan(sum, sh, &tot);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int64_t idx = (int64_t)threadIdx.x * 4 + k;
+            if (idx < nseg) wf.bsum[idx] = ex;
+            ex += v[k];
+          }
+        }
+        if (!grid_sync(wf.gsync, a.err)) return;
+        const int64_t cnt = (int64_t)__ldcg(wf.count + cur);
+        for (int64_t j = gtid; j < cnt; j += gstride) {
+          const unsigned k = __ldcg(wf.key + j);
+          const int64_t d = (int64_t)__ldcg(wf.boff + k) + __ldcg(wf.bsum + (k >> 12)) + __ldcg(wf.rank + j);
+          if (d >= cnt) atomicOr(a.err, ERR_QUEUE);
+          else wf.perm[d] = (unsigned)j;
+        }
+      }
+      if (keys_next)
+        for (int64_t k = gtid; k < wf.n_keys; k += gstride) wf.bcount[k] = 0u;
+      if (gtid == 0) wf.count[1 - cur] = 0u;
+      if (!grid_sync(wf.gsync, a.err)) return;
+      if (cur == 0) pass_range_q<NBT, HE, HEAT, 0>(a, t, wf, S, sorted_now, keys_next, curve);
+      else pass_range_q<NBT, HE, HEAT, 1>(a, t, wf, S, sorted_now, keys_next, curve);
+      if (!grid_sync(wf.gsync, a.err)) return;
+      if (threadIdx.x == 0) {
+        s_cur = 1 - s_cur;
+        s_p = s_p + 1;
+      }
+      __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && __ldcg(wf.count + s_cur) != 0u) atomicOr(a.err, ERR_WATCHDOG);
+    if (!grid_sync(wf.gsync, a.err)) return;
+    if (threadIdx.x == 0) s_g0 = s_g0 + wf.cap;
+    __syncthreads();
+  }
 }
 
 int g_num_sms = 0;
@@ -1102,6 +1350,17 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
     (*ev_used)++;
   };
   if (a.total_packets <= 0) return 0;
+  if (a.any_periodic) {
+    // periodic boxes: one thread per packet, traced to the end of its c dt
+    int64_t blocks = (a.total_packets + block - 1) / block;
+    if (blocks > (int64_t)1 << 30) blocks = (int64_t)1 << 30;
+    WFArgs w = wf_args(wf, 0, false, false);
+    tic();
+    k_emit_mixed<NBT, HE, HEAT, 3, true><<<(unsigned)blocks, block, 0, s>>>(a, t, w, 0, a.total_packets,
+                                                                         max_iter, max_iter);
+    toc();
+    return 1;
+  }
   if (!o.wavefront || wf->cap == 0) {
     // one thread per packet, traced to the end
     WFArgs w = wf_args(wf, 0, false, false);
@@ -1172,6 +1431,30 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
   // passes, which read the queue in sorted order
   int passes = (max_iter + S - 1) / S + 1;
   if (o.pass_limit > 0 && o.pass_limit < passes) passes = o.pass_limit;
+  if (o.persistent && wf->gsync) {
+    // one cooperative launch for the whole step (all blocks resident)
+    static int per_sm[2] = {0, 0};
+    const int ci = o.reg_cap ? 1 : 0;
+    if (!per_sm[ci]) {
+      if (o.reg_cap)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ci], k_wavefront<NBT, HE, HEAT, 4>, 256, 0);
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ci], k_wavefront<NBT, HE, HEAT, 3>, 256, 0);
+    }
+    if (per_sm[ci] < 1) return -1;
+    cudaMemsetAsync(wf->gsync, 0, 2 * sizeof(unsigned), s);
+    WF wv = *wf;
+    StepArgs av = a;
+    BinTables tv = t;
+    int Sv = S, Rv = R, pv = passes, cv = o.sort_curve, mv = max_iter;
+    void* args[] = {&av, &tv, &wv, &Sv, &Rv, &pv, &cv, &mv};
+    tic();
+    const cudaError_t e = o.reg_cap
+        ? cudaLaunchCooperativeKernel((const void*)k_wavefront<NBT, HE, HEAT, 4>, num_sms() * per_sm[ci], 256, args, 0, s)
+        : cudaLaunchCooperativeKernel((const void*)k_wavefront<NBT, HE, HEAT, 3>, num_sms() * per_sm[ci], 256, args, 0, s);
+    toc();
+    return e == cudaSuccess ? 1 : -1;
+  }
   const int nscan = (int)((wf->n_keys + 4095) / 4096);
   // the pass p (p >= 1) reads in sorted order when R > 0 and p % R == 0
   auto sorted_pass = [&](int p) { return p >= 1 && p < passes && R > 0 && (p % R) == 0; };
@@ -1254,6 +1537,7 @@ int launch_trace_mixed_external(const StepArgs& a, const BinTables& t, const cra
   oo.wavefront = 1;
   oo.resort_interval = -1;     // no sort keys without their workspace
   oo.tile = 0;
+  oo.persistent = 0;           // no grid barrier word either
   return launch_trace_mixed(a, t, oo, &wf, max_iter, s, nullptr, nullptr);
 }
 
@@ -1273,6 +1557,7 @@ void* wavefront_create(int64_t cap, int64_t n_keys, int nb, cudaError_t* err) {
     if (e == cudaSuccess) e = cudaMalloc(&w->boff, sizeof(unsigned) * n_keys);
     if (e == cudaSuccess) e = cudaMalloc(&w->bsum, sizeof(unsigned) * 1024);
     if (e == cudaSuccess) e = cudaMalloc(&w->items, sizeof(uint2) * (n_keys / 8 + cap / 2048 + 2));
+    if (e == cudaSuccess) e = cudaMalloc(&w->gsync, 2 * sizeof(unsigned));
   }
   if (err) *err = e;
   if (e != cudaSuccess) {
@@ -1286,7 +1571,7 @@ void wavefront_destroy(void* p) {
   WF* w = (WF*)p;
   if (!w) return;
   void* ptrs[] = {w->count, w->key, w->rank, w->perm, w->bcount, w->boff, w->bsum, w->items,
-                  w->rec[0], w->rec[1]};
+                  w->gsync, w->rec[0], w->rec[1]};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete w;

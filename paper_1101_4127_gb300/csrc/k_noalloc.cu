@@ -98,7 +98,6 @@ extern "C" crash_status crash_transport_noalloc(const crash_grid_desc* grid, int
                                     "step into calls over packet windows of a context instead");
   const uint64_t Ns = packets_per_step / (uint64_t)n_src;
   if (seg_per_pass < 0) return fail(CRASH_ERR_ARG, "seg_per_pass must be >= 0");
-  double mx = 0.0;
   for (int s = 0; s < n_src; ++s) {
     const double* p = pos_cells + 3 * s;
     if (!(p[0] >= 0 && p[0] < d.nx && p[1] >= 0 && p[1] < d.ny && p[2] >= 0 && p[2] < d.nz))
@@ -106,7 +105,6 @@ extern "C" crash_status crash_transport_noalloc(const crash_grid_desc* grid, int
     if (!(ndot[s] >= 0) || !isfinite(ndot[s])) return fail(CRASH_ERR_ARG, "source rates must be finite and >= 0");
     for (int j = 0; j < n_bins; ++j)
       if (!(bin_frac[(size_t)s * n_bins + j] >= 0)) return fail(CRASH_ERR_ARG, "bin fractions must be >= 0");
-    mx = std::max(mx, ndot[s]);
   }
   for (int j = 0; j < n_bins; ++j)
     if (!(bin_eV[j] > 0)) return fail(CRASH_ERR_ARG, "bin energies must be positive");
@@ -147,7 +145,9 @@ extern "C" crash_status crash_transport_noalloc(const crash_grid_desc* grid, int
   m.src_off = 0;
   m.n_src = n_src;
   m.heatF = heatF;
-  m.ndot_max = mx;
+  double sum = 0.0;
+  for (int s = 0; s < n_src; ++s) sum += ndot[s];
+  m.ndot_sum = sum;
   m.pkts_per_src = Ns;
   m.win_lo = 0;
   m.win_hi = (uint32_t)Ns;

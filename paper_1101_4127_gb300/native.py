@@ -29,11 +29,12 @@ F_REC_HI, F_REC_HEI, F_REC_HEII = 11, 12, 13
 
 EXPORTED = [
     "crash_default_opts", "crash_init_grid", "crash_init_batch", "crash_add_sources",
-    "crash_add_sources_box", "crash_set_options", "crash_step", "crash_step_batch",
+    "crash_add_sources_box", "crash_set_options", "crash_get_options", "crash_step", "crash_step_batch",
     "crash_read_fields", "crash_read_fields_box", "crash_write_fields", "crash_write_fields_box",
     "crash_set_step_index", "crash_sync", "crash_kernel_time", "crash_reset_kernel_time",
     "crash_stream", "crash_launch_count", "crash_autotune", "crash_free", "crash_last_error",
     "crash_transport_noalloc", "crash_noalloc_last_error", "crash_checkpoint",
+    "crash_deposits_device", "crash_read_deposits", "crash_write_deposits", "crash_chemistry",
 ]
 CKPT_SAVE, CKPT_RESTORE_STATE, CKPT_RESTORE = 0, 1, 2
 
@@ -46,7 +47,7 @@ class crash_grid_desc(C.Structure):
                 ("x_HII0", C.c_double), ("x_HeII0", C.c_double), ("x_HeIII0", C.c_double),
                 ("T0", C.c_double), ("isothermal", C.c_int), ("caseB", C.c_int),
                 ("z_compton", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int),
-                ("f_rec", C.c_double)]
+                ("f_rec", C.c_double), ("coupling", C.c_int), ("periodic", C.c_int)]
 
 
 class crash_run_opts(C.Structure):
@@ -55,7 +56,7 @@ class crash_run_opts(C.Structure):
                 ("block_size", C.c_int), ("seg_per_iter", C.c_int), ("resort_interval", C.c_int),
                 ("wavefront", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
                 ("reg_cap", C.c_int), ("tile", C.c_int), ("pass_limit", C.c_int),
-                ("sort_curve", C.c_int)]
+                ("sort_curve", C.c_int), ("chunk_packets", C.c_int), ("persistent", C.c_int)]
 
 
 def library_path() -> str:
@@ -81,6 +82,7 @@ def lib(build_if_missing: bool = True):
             L.crash_add_sources.argtypes = [P, C.c_int, dp, dp, C.c_int, dp, dp]
             L.crash_add_sources_box.argtypes = [P, C.c_int, C.c_int, dp, dp, C.c_int, dp, dp]
             L.crash_set_options.argtypes = [P, C.POINTER(crash_run_opts)]
+            L.crash_get_options.argtypes = [P, C.POINTER(crash_run_opts)]
             L.crash_step.argtypes = [P, C.c_double, C.c_uint64]
             L.crash_step_batch.argtypes = [P, C.c_double, C.POINTER(C.c_uint64)]
             L.crash_read_fields.argtypes = [P, C.c_int, P]
@@ -102,6 +104,10 @@ def lib(build_if_missing: bool = True):
             L.crash_transport_noalloc.argtypes = [
                 C.POINTER(crash_grid_desc), C.c_int, dp, dp, C.c_int, dp, dp, C.c_double, C.c_uint64,
                 C.c_uint64, C.c_int, P, P, C.POINTER(C.c_int64), P]
+            L.crash_deposits_device.argtypes = [P, C.c_int, C.POINTER(P), C.POINTER(C.c_int64)]
+            L.crash_read_deposits.argtypes = [P, C.c_int, P]
+            L.crash_write_deposits.argtypes = [P, C.c_int, P]
+            L.crash_chemistry.argtypes = [P, C.c_double]
             L.crash_noalloc_last_error.argtypes = []
             L.crash_noalloc_last_error.restype = C.c_char_p
             L.crash_free.argtypes = [P]
@@ -147,6 +153,8 @@ def make_desc(box, precision=CRASH_FP64_PLAIN, keep=None):
     d.isothermal, d.caseB, d.z_compton, d.seed = box.isothermal, box.caseB, box.z_compton, box.seed
     d.precision = precision
     d.f_rec = getattr(box, "f_rec", 0.0)
+    d.coupling = getattr(box, "coupling", 0)
+    d.periodic = getattr(box, "periodic", 0)
     return d
 
 
@@ -190,6 +198,12 @@ class Grid:
             setattr(o, k, v)
         self._check(self.L.crash_set_options(self.ctx, C.byref(o)))
 
+    def get_options(self):
+        """The context's current options as a dict (field name -> value)."""
+        o = crash_run_opts()
+        self._check(self.L.crash_get_options(self.ctx, C.byref(o)))
+        return {k: getattr(o, k) for k, _ in crash_run_opts._fields_}
+
     def step(self, dt_s, packets):
         if isinstance(packets, (list, tuple, np.ndarray)):
             arr = (C.c_uint64 * len(packets))(*[int(p) for p in packets])
@@ -222,6 +236,27 @@ class Grid:
     def write(self, field, arr, box=0):
         a = np.ascontiguousarray(arr, np.float64).reshape(-1)
         self._check(self.L.crash_write_fields_box(self.ctx, box, field, a.ctypes.data_as(C.c_void_p)))
+
+    def deposits_device(self, box=0):
+        """Device address and cell count of a box's deposits, uint64[cells][4]."""
+        p, n = C.c_void_p(), C.c_int64()
+        self._check(self.L.crash_deposits_device(self.ctx, box, C.byref(p), C.byref(n)))
+        return p.value, n.value
+
+    def read_deposits(self, box=0):
+        """The box's deposits as int64[cells, 4] (H I, He I, He II, heat)."""
+        nx, ny, nz = self.boxes[box].shape_xyz
+        out = np.zeros((nx * ny * nz, 4), np.int64)
+        self._check(self.L.crash_read_deposits(self.ctx, box, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def write_deposits(self, dep, box=0):
+        a = np.ascontiguousarray(dep, np.int64).reshape(-1, 4)
+        self._check(self.L.crash_write_deposits(self.ctx, box, a.ctypes.data_as(C.c_void_p)))
+
+    def chemistry(self, dt_s):
+        """The per-cell update of the last (transport-only) step."""
+        self._check(self.L.crash_chemistry(self.ctx, float(dt_s)))
 
     def kernel_time(self):
         ms = C.c_double(0)

@@ -33,14 +33,16 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_struct_layouts_match_header(tmp_path):
     probe = tmp_path / "probe.c"
     probe.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crash.h"\n'
-                     'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(crash_grid_desc),'
+                     'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(crash_grid_desc),'
                      ' sizeof(crash_run_opts), offsetof(crash_grid_desc, f_rec),'
-                     ' offsetof(crash_run_opts, sort_curve));return 0;}\n')
+                     ' offsetof(crash_run_opts, sort_curve), offsetof(crash_grid_desc, periodic),'
+                     ' offsetof(crash_run_opts, chunk_packets));return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HDR), str(probe), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [C.sizeof(native.crash_grid_desc), C.sizeof(native.crash_run_opts),
-                   native.crash_grid_desc.f_rec.offset, native.crash_run_opts.sort_curve.offset]
+                   native.crash_grid_desc.f_rec.offset, native.crash_run_opts.sort_curve.offset,
+                   native.crash_grid_desc.periodic.offset, native.crash_run_opts.chunk_packets.offset]
 
 
 def test_argument_errors_are_status_codes():
@@ -61,7 +63,15 @@ def test_argument_errors_are_status_codes():
     d.f_rec = 1.5                     # the re-emission threshold is a fraction
     assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
     d.f_rec = 0.0
+    d.coupling = 2                    # 0 or 1
+    assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
+    d.coupling, d.periodic = 0, 3
+    assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
+    d.periodic = 0
     assert L.crash_step(None, 1.0, 1) == native.CRASH_ERR_ARG
+    assert L.crash_chemistry(None, 1.0) == native.CRASH_ERR_ARG
+    p = C.c_void_p()
+    assert L.crash_deposits_device(None, 0, C.byref(p), None) == native.CRASH_ERR_ARG
     assert L.crash_free(None) == native.CRASH_ERR_ARG
     o = native.default_opts()
     assert o.chemistry == 1 and o.pkt_end == 0xFFFFFFFF and o.cool_mask == 63

@@ -37,10 +37,14 @@ def test_mixed_budget_closes_and_launch_shapes_agree_bit_for_bit():
     dt = 0.01 * inputs.MYR_S
     ref = _fields(_run(box, P, 2, dt, wavefront=0))
     assert ref[-1][0] == ref[-1][1] + ref[-1][2]
+    # the wavefront in one persistent launch per step (default) and in one
+    # launch per pass and re-sort phase
     for S, R, cap in [(1, -1, 0), (7, 1, 1), (16, 2, 0), (64, 3, 1), (5, 1, 0)]:
-        got = _fields(_run(box, P, 2, dt, wavefront=1, seg_per_iter=S, resort_interval=R, reg_cap=cap))
-        for a, b in zip(ref, got):
-            assert np.array_equal(a, b), (S, R, cap)
+        for persistent in (1, 0):
+            got = _fields(_run(box, P, 2, dt, wavefront=1, seg_per_iter=S, resort_interval=R, reg_cap=cap,
+                               persistent=persistent))
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), (S, R, cap, persistent)
     got = _fields(_run(box, P, 2, dt, wavefront=1, tile=1))      # shared-memory tile passes
     for a, b in zip(ref, got):
         assert np.array_equal(a, b), "tile"
@@ -62,13 +66,19 @@ def test_tile_passes_dense_tiles_bit_for_bit():
 
 
 def test_mixed_graph_replay_identical():
+    """A step captured in a CUDA graph (the persistent cooperative launch by
+    default, or the launch-per-pass sequence) replays the same bits, and the
+    persistent step is a handful of launches."""
     box = small_hhe_box((12, 12, 12), n_src=2, seed=102)
     P = 2 * 2000
     dt = 0.01 * inputs.MYR_S
     a = _fields(_run(box, P, 3, dt))
-    b = _fields(_run(box, P, 3, dt, use_graph=1))
-    for x, y in zip(a, b):
-        assert np.array_equal(x, y)
+    for persistent in (1, 0):
+        g = _run(box, P, 3, dt, use_graph=1, persistent=persistent)
+        for x, y in zip(a, _fields(g)):
+            assert np.array_equal(x, y), persistent
+        if persistent:
+            assert g.launch_count() <= 3 * 8, g.launch_count()
 
 
 def test_mixed_batch_equals_separate_boxes():
@@ -157,6 +167,13 @@ def test_mixed_full_size_512_window_against_oracle():
     a = g.read(native.F_DEP_HI).astype(np.float64)
     b = o.read(oracle.F_DEP_HI).astype(np.float64)
     assert abs(a.sum() - b.sum()) <= 1e-5 * b.sum()
+    # cell by cell, all four deposit fields, where the oracle's deposit is at
+    # least 1e-3 of its largest
+    from test_mixed_accuracy_gpu import _deposit_stats, _report
+    dep = _deposit_stats(g, o)
+    _report(w.name + "_window", {"packet_ids": [0, 2], "deposits": dep})
+    for nm, d in dep.items():
+        assert d["sum_rel"] < 1e-4 and d["median_rel"] < 1e-4, (nm, d)
 
 
 def test_batch_64_recipe_graph_equals_separate_boxes():
