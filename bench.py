@@ -45,6 +45,8 @@ def workload(name):
     if name == "hhe_bb_128":
         w = inputs.hhe_blackbody_128()
         return w, native.CRASH_FP64_PLAIN
+    if name == "hhe_bb_128_mixed":       # the same workload in the mixed form
+        return inputs.hhe_blackbody_128(), native.CRASH_MIXED
     if name == "stromgren_32":
         return inputs.stromgren_32(), native.CRASH_FP64_PLAIN
     if name == "lognormal_128":
@@ -144,82 +146,90 @@ class ClockSampler:
 
 
 def traffic_for(workload_name, kernel_src):
-    """DRAM bytes per crossing of the dominant kernel from the committed ncu
-    summary (profiles/traffic.md), if taken on the current kernel source."""
+    """DRAM bytes per crossing of the transport from the committed ncu summary
+    (profiles/traffic.md), if taken on the current kernel source; the row of
+    the workload itself, else the row of the smaller case it names."""
     p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
-        return None, None
+        return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:12]
     for ln in open(p):
         c = [x.strip() for x in ln.strip().strip("|").split("|")]
-        if len(c) >= 4 and c[0] == workload_name:
-            if c[1] == sha:
-                return float(c[2]), float(c[3])   # dram bytes per launch, crossings per launch
-            return None, None
-    return None, None
+        if len(c) >= 3 and workload_name in [x.strip() for x in c[0].split(",")] and c[1] == sha:
+            try:
+                return float(c[2])                # DRAM bytes per crossing
+            except ValueError:
+                return None
+    return None
 
 
 # ---------------------------------------------------------------- reference arm
+_ORACLE_CACHE = {}
+
+
 def oracle_sample(w, seconds=15.0):
     """Time the CPU oracle (one core) on a bounded sample of one step of the
-    workload and extrapolate to the whole step: the transport of packet ids
-    [0, K) of every source (K grown until it takes about seconds/2), plus the
-    per-cell chemistry of the step timed on the grid itself when it has at
-    most 128^3 cells, else on a 128^3 corner of it.  Returns
-    (crossings/s, description, seconds spent)."""
+    workload and extrapolate to the whole step.
+
+    Transport: packet ids [0, K) of every source, K grown until the step
+    takes about seconds/2 beyond a step with no packets (the fixed per-step
+    cost of freezing the absorbers is timed alone and counted once, not
+    scaled with the packets).  Chemistry: the per-cell update of that step on
+    every S-th cell of the whole grid, with the window's deposits scaled by
+    Ns/K to those of the full step, less the same step without chemistry,
+    scaled by S.  Returns (crossings/s, description, seconds spent)."""
     import oracle
-    from paper_1101_4127_gb300 import inputs
     box = w.boxes[0]
     P = w.packets_per_step[0]
     Ns = P // box.n_src
-    K = 1
+    ncell = int(np.prod(box.shape_xyz))
     spent = 0.0
-    while True:
+    # one oracle grid per workload and process; every timed step starts from
+    # the workload's initial state and step index
+    if _ORACLE_CACHE.get("name") != w.name:
+        _ORACLE_CACHE.clear()
         o = oracle.OracleGrid.from_box(box)
+        fields = (oracle.F_XHII, oracle.F_XHEII, oracle.F_XHEIII, oracle.F_T)
+        _ORACLE_CACHE.update(name=w.name, grid=o, state=[(f, o.read(f)) for f in fields])
+    o = _ORACLE_CACHE["grid"]
+
+    def timed_step(K):
         o.set_options(chemistry=0, pkt_begin=0, pkt_end=K)
+        o.set_step_index(0)
         t0 = time.perf_counter()
         o.step(w.dt_s, P)
-        t_tr = time.perf_counter() - t0
-        spent += t_tr
-        cross = int(o.read(oracle.F_BUDGET)[3])
-        o.close()
+        t = time.perf_counter() - t0
+        return t, int(o.read(oracle.F_BUDGET)[3])
+
+    t_fixed, _ = timed_step(0)
+    spent += t_fixed
+    K = 1
+    while True:
+        t, cross = timed_step(K)
+        spent += t
+        t_tr = max(t - t_fixed, 1e-6)
         if t_tr > seconds / 2 or K >= Ns:
             break
-        K = min(Ns, max(K * 2, int(K * (seconds / 2) / max(t_tr, 1e-3))))
-    # chemistry of one step on (a corner of) the grid, with that step's deposits
-    m = min(box.n, 128)
-    sub = box
-    if m < box.n:
-        import copy
-        sub = copy.copy(box)
-        sub.n = m
-        sub.nH = np.ascontiguousarray(box.nH[:m, :m, :m]) if box.nH is not None else None
-        keep = np.all(box.src_pos < m, axis=1)
-        if not keep.any():
-            keep[:] = False
-            keep[0] = True
-            sub.src_pos = np.full((1, 3), 0.5 * m)
-        else:
-            sub.src_pos = box.src_pos[keep]
-        sub.src_ndot = box.src_ndot[keep][: len(sub.src_pos)]
-        sub.bin_frac = box.bin_frac[keep][: len(sub.src_pos)]
-    o = oracle.OracleGrid.from_box(sub)
-    Psub = sub.src_ndot.shape[0] * max(1, min(Ns, 64))
-    o.set_options(chemistry=0)
-    o.step(w.dt_s, Psub)
-    o.set_options(chemistry=1, pkt_begin=0, pkt_end=0)
+        # grow at most 8x per trial: a short trial's time is mostly noise
+        K = min(Ns, K * 8, max(K * 2, int(K * (seconds / 2) / t_tr)))
+    # chemistry of that step alone on every stride-th cell, deposits scaled
+    # to the full step (the state is put back afterwards)
+    stride = max(1, ncell // 200_000)
+    o.set_chem_sample(stride, Ns / K)
     t0 = time.perf_counter()
-    o.step(w.dt_s, Psub)               # chemistry only (empty packet window)
+    o.chemistry(w.dt_s)
     t_chem = time.perf_counter() - t0
     spent += t_chem
-    o.close()
-    ncell = box.n ** 3
-    t_step = t_tr * (Ns / K) + t_chem * (ncell / m ** 3)
+    o.set_chem_sample(1, 1.0)
+    for f, a in _ORACLE_CACHE["state"]:
+        o.write(f, a)
+    t_step = t_fixed + t_tr * (Ns / K) + t_chem * stride
     cross_step = cross * (Ns / K)
     rate = cross_step / t_step
     desc = (f"one step of {w.name}: transport of packet ids [0,{K}) of each of the {box.n_src} "
-            f"sources ({cross} crossings, {t_tr:.2f} s) scaled to {Ns} per source, plus chemistry "
-            f"timed on {m}^3 cells ({t_chem:.2f} s) scaled to {box.n}^3")
+            f"sources ({cross} crossings, {t_tr:.2f} s beyond the {t_fixed:.2f} s fixed cost) scaled "
+            f"to {Ns} per source, plus the per-cell update of every {stride}-th of the {ncell} cells "
+            f"with the full step's deposits ({t_chem:.2f} s) scaled to all cells")
     return rate, desc, spent
 
 
@@ -285,7 +295,8 @@ def run_crash(args):
     ncell_all = sum(bx.n ** 3 for bx in boxes)
     g = native.Grid(boxes, prec)
     graph = bool(args.graph)
-    g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0)
+    pers = {"persistent": 1, "per-pass": 0}.get(args.launch, 1)
+    g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0, persistent=pers)
     stream = torch.cuda.ExternalStream(g.stream(), device=dev)
     state_bytes = ncell_all * (4 + 4 * 8 + 32 + (32 if prec == native.CRASH_FP64_PLAIN else 16))
     l2_bytes = 129 * 2**20
@@ -324,10 +335,19 @@ def run_crash(args):
             g.sync()
             # block, crossings per pass, re-sort, register cap, tiles, key curve
             tuned = g.autotune(w.dt_s, Plist)
+            if args.launch == "auto":           # the autotuner also chose the launch style
+                pers = int(g.get_options()["persistent"])
             tuned_kw.update(block_size=tuned[0], seg_per_iter=tuned[1], resort_interval=tuned[2],
-                            reg_cap=tuned[3], tile=tuned[4], sort_curve=tuned[5])
+                            reg_cap=tuned[3], tile=tuned[4], sort_curve=tuned[5], persistent=pers)
             g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0, **tuned_kw)
     g.sync()
+    if prec == native.CRASH_FP64_PLAIN:
+        launch_style = "one thread per packet"
+    elif g.get_options()["tile"]:
+        launch_style = "tile passes"
+    else:
+        launch_style = "one persistent launch per step" if g.get_options()["persistent"] \
+            else "one launch per pass"
     g.reset_kernel_time()
     tot0 = totals()
     launches0 = g.launch_count()
@@ -371,11 +391,11 @@ def run_crash(args):
     achieved = (crossings * bpc) / (kms * 1e-3) / 1e9 if kms > 0 else None
     ksrc = os.path.join(ROOT, "paper_1101_4127_gb300", "csrc",
                         "k_fp64.cu" if prec == native.CRASH_FP64_PLAIN else "k_mixed.cu")
-    dram_per_launch, cross_per_launch = traffic_for(args.workload, ksrc)
+    dram_per_crossing = traffic_for(args.workload, ksrc)
     traffic = None
-    if dram_per_launch is not None and klaunches:
-        # scale the captured launch to this run's average launch by crossings
-        traffic = dram_per_launch * (crossings / klaunches) / cross_per_launch
+    if dram_per_crossing is not None and klaunches:
+        # DRAM bytes of this run's average transport launch
+        traffic = dram_per_crossing * crossings / klaunches
 
     # end-to-end through the C ABI with host buffers (pinned): every step
     # uploads its inputs (the sources, and for the held thin state the four
@@ -424,26 +444,36 @@ def run_crash(args):
 
     fp64 = None
     if rank == 0 and prec == native.CRASH_MIXED and not args.no_fp64 and not batch:
-        # the FP64 form on the same inputs, transport only, over a window of
-        # packet ids of every source (the FP64 pipe of this GPU is narrow)
+        # the FP64 form and the mixed form on the same inputs: the transport of
+        # the same window of packet ids of every source, the same (second)
+        # step from the same initial state, kernel time of each (the FP64
+        # pipe of this GPU is narrow, so the window is small)
         g.close()
         g = None
-        g64 = native.Grid(box, native.CRASH_FP64_PLAIN)
         Ns = P // box.n_src
         K = max(1, min(Ns, (1 << 21) // box.n_src))
-        g64.set_options(chemistry=0, timing=1, pkt_begin=0, pkt_end=K)
-        g64.step(w.dt_s, P)
-        g64.sync()
-        g64.reset_kernel_time()
-        t0 = g64.read(native.F_TOTALS)
-        g64.step(w.dt_s, P)
-        g64.sync()
-        t1 = g64.read(native.F_TOTALS)
-        ms64, _ = g64.kernel_time()
-        fp64 = {"value": float(t1[3] - t0[3]) / (ms64 * 1e-3), "unit": "crossings/s",
+
+        def window_rate(precision, **opts):
+            gw = native.Grid(box, precision)
+            gw.set_options(chemistry=0, timing=1, pkt_begin=0, pkt_end=K, **opts)
+            gw.step(w.dt_s, P)
+            gw.sync()
+            gw.reset_kernel_time()
+            t0 = gw.read(native.F_TOTALS)
+            gw.step(w.dt_s, P)
+            gw.sync()
+            t1 = gw.read(native.F_TOTALS)
+            ms_w, _ = gw.kernel_time()
+            gw.close()
+            return float(t1[3] - t0[3]) / (ms_w * 1e-3), int(t1[3] - t0[3])
+
+        r64, c64 = window_rate(native.CRASH_FP64_PLAIN)
+        rmx, cmx = window_rate(native.CRASH_MIXED, **{k: v for k, v in tuned_kw.items()})
+        fp64 = {"value": r64, "unit": "crossings/s",
                 "sample": f"transport of packet ids [0,{K}) of each of the {box.n_src} sources, "
-                          f"first step, kernel time", "crossings": int(t1[3] - t0[3])}
-        g64.close()
+                          f"second step, kernel time", "crossings": c64,
+                "mixed_same_sample": {"value": rmx, "unit": "crossings/s", "crossings": cmx},
+                "mixed_over_fp64": rmx / r64}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -462,6 +492,7 @@ def run_crash(args):
                        "sources": sum(bx.n_src for bx in boxes),
                        "packets_per_step": sum(Plist), "bins": len(box.bin_eV),
                        "cuda_graph": graph,
+                       "transport_launch": launch_style,
                        "precision": "fp64" if prec == native.CRASH_FP64_PLAIN else "mixed",
                        "l2": "flushed between steps (256 MiB write)" if flush is not None
                              else "state larger than L2",
@@ -514,6 +545,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--packets", type=int, default=0, help="override packets per step (small cases)")
+    ap.add_argument("--launch", default="auto", choices=["auto", "persistent", "per-pass"],
+                    help="transport launch style: one persistent launch per step, one launch per "
+                         "wavefront pass, or (auto) the autotuner's choice (persistent when not tuned)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -42,12 +42,14 @@ def test_bytes_per_crossing_follow_the_payloads():
 
 
 def test_traffic_table_rows_parse():
+    """Rows: the workloads a capture stands for | k_mixed.cu sha256[:12] |
+    DRAM bytes per crossing | the capture it came from."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     rows = [l for l in open(path) if l.startswith("| lognormal")]
     assert rows
     for l in rows:
         c = [x.strip() for x in l.strip().strip("|").split("|")]
-        assert re.fullmatch(r"[0-9a-f]{12}", c[1]) and float(c[2]) > 0 and float(c[3]) > 0
+        assert re.fullmatch(r"[0-9a-f]{12}", c[1]) and 0 < float(c[2]) < 1000 and c[3]
     ksrc = os.path.join(ROOT, "paper_1101_4127_gb300", "csrc", "k_mixed.cu")
-    dram, cross = bench.traffic_for("lognormal_512_thin", ksrc)
-    assert (dram is None and cross is None) or (dram > 0 and cross > 0)
+    per = bench.traffic_for("lognormal_512_thin", ksrc)
+    assert per is None or per > 0
