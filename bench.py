@@ -475,6 +475,40 @@ def run_crash(args):
                 "mixed_same_sample": {"value": rmx, "unit": "crossings/s", "crossings": cmx},
                 "mixed_over_fp64": rmx / r64}
 
+    # a batch against the same boxes stepped one at a time, each in its own
+    # context (the launches of every box's step issued in turn; host clock
+    # around K steps of all boxes, the device synchronised on both sides)
+    one_by_one = None
+    if rank == 0 and batch and args.one_by_one:
+        if g is not None:
+            g.close()
+            g = None
+        singles = []
+        for bx, pb in zip(boxes, Plist):
+            gs = native.Grid(bx, prec)
+            gs.set_options(use_graph=1 if graph else 0, **{k: v for k, v in tuned_kw.items()})
+            gs.step(w.dt_s, pb)
+            singles.append((gs, pb))
+        for gs, _ in singles:
+            gs.sync()
+        c0 = sum(int(gs.read(native.F_TOTALS)[3]) for gs, _ in singles)
+        l0 = sum(gs.launch_count() for gs, _ in singles)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for gs, pb in singles:
+                gs.step(w.dt_s, pb)
+        for gs, _ in singles:
+            gs.sync()
+        t_one = time.perf_counter() - t0
+        c1 = sum(int(gs.read(native.F_TOTALS)[3]) for gs, _ in singles)
+        l1 = sum(gs.launch_count() for gs, _ in singles)
+        for gs, _ in singles:
+            gs.close()
+        one_by_one = {"value": (c1 - c0) / t_one, "unit": "crossings/s",
+                      "ms_per_step": 1e3 * t_one / args.steps,
+                      "launches_per_step": (l1 - l0) / args.steps,
+                      "how": f"{len(boxes)} contexts, one per box, stepped in turn (host clock)"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, desc, _ = oracle_sample(w, seconds=args.ref_seconds)
@@ -508,6 +542,7 @@ def run_crash(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "fp64_plain": fp64,
+            "one_by_one": one_by_one,
             "autotuned": {"block": tuned[0], "crossings_per_pass": tuned[1],
                           "resort_interval": tuned[2], "reg_cap": tuned[3],
                           "tile": tuned[4], "sort_curve": ["morton", "hilbert"][tuned[5]]}
@@ -545,6 +580,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--packets", type=int, default=0, help="override packets per step (small cases)")
+    ap.add_argument("--one-by-one", action="store_true",
+                    help="batched workloads: also time the same boxes stepped one at a time")
     ap.add_argument("--launch", default="auto", choices=["auto", "persistent", "per-pass"],
                     help="transport launch style: one persistent launch per step, one launch per "
                          "wavefront pass, or (auto) the autotuner's choice (persistent when not tuned)")

@@ -403,6 +403,7 @@ void cross_sections(int nb, const double* E, BinTables& t, int& heatF) {
       t.wheat[s][j] = E[j] >= kEth[s] ? ldexp(E[j] - kEth[s], -heatF) : 0.0;
       t.sigma32[s][j] = (float)t.sigma[s][j];
       t.wheat32[s][j] = (float)t.wheat[s][j];
+      t.sw32[s][j] = t.sigma32[s][j] * t.wheat32[s][j];
     }
   for (int s = 0; s < 3; ++s) {
     t.sigma32_max[s] = 0.f;

@@ -68,6 +68,7 @@ struct BinTables {
   float sigma32[3][CRASH_MAX_BINS];
   float wheat32[3][CRASH_MAX_BINS];
   float sigma32_max[3];              // largest sigma32 of each species over the bins
+  float sw32[3][CRASH_MAX_BINS];     // sigma32 * wheat32 (FP32 product): heating weight per unit t_s
 };
 
 struct StepArgs {

@@ -109,17 +109,41 @@ __device__ __forceinline__ long long float_to_ll(float x) {
   return (long long)(((unsigned long long)hi << 32) | lo);
 }
 
-// (1 - exp(-tau)) / tau for 0 < tau < 0.5 by its Taylor series to tau^7
-// (truncation below 2e-8 relative)
+// rint of the three per-cell shares x1, x2, xh (each at most about the
+// cell's absorbed total Au): with Au below 2^31 all three fit the 32-bit
+// conversion, which is then the whole rounding
+__device__ __forceinline__ void round_shares(long long Au, float x1, float x2, float xh, long long& a1,
+                                             long long& a2, long long& h) {
+  if ((unsigned long long)Au < 0x80000000ull) {
+    a1 = (long long)__float2uint_rn(x1);
+    a2 = (long long)__float2uint_rn(x2);
+    h = (long long)__float2uint_rn(xh);
+  } else {
+    a1 = float_to_ll(x1);
+    a2 = float_to_ll(x2);
+    h = float_to_ll(xh);
+  }
+}
+
+// (1 - exp(-tau)) / tau for 0 <= tau <= 0.5: a degree-5 polynomial fitted
+// for the smallest largest relative error on [0, 0.5] (Lawson's iteration
+// on 4000 Chebyshev-spaced points).  With its coefficients rounded to FP32
+// the polynomial is within 7e-9 of the function; evaluated in FP32 by
+// Horner's rule the result is within 5.4e-8 (the Taylor series to tau^7
+// gave 5.7e-8 with two more steps).  tests/test_series_poly.py checks both.
+#define CRASH_AOT_C0 1.0f
+#define CRASH_AOT_C1 -0.4999998211860657f
+#define CRASH_AOT_C2 0.16666224598884583f
+#define CRASH_AOT_C3 -0.041629090905189514f
+#define CRASH_AOT_C4 0.008187386207282543f
+#define CRASH_AOT_C5 -0.0011216348502784967f
 __device__ __forceinline__ float absorbed_over_tau(float tau) {
-  float p = -1.0f / 40320.0f;
-  p = fmaf(p, tau, 1.0f / 5040.0f);
-  p = fmaf(p, tau, -1.0f / 720.0f);
-  p = fmaf(p, tau, 1.0f / 120.0f);
-  p = fmaf(p, tau, -1.0f / 24.0f);
-  p = fmaf(p, tau, 1.0f / 6.0f);
-  p = fmaf(p, tau, -0.5f);
-  p = fmaf(p, tau, 1.0f);
+  float p = CRASH_AOT_C5;
+  p = fmaf(p, tau, CRASH_AOT_C4);
+  p = fmaf(p, tau, CRASH_AOT_C3);
+  p = fmaf(p, tau, CRASH_AOT_C2);
+  p = fmaf(p, tau, CRASH_AOT_C1);
+  p = fmaf(p, tau, CRASH_AOT_C0);
   return p;
 }
 
@@ -203,47 +227,51 @@ __device__ __forceinline__ unsigned absorb_lane(unsigned m, float Nf, float tau,
 }
 
 // cell_attenuate for an even number of bins, two bins per packed
-// instruction: the optical depths, the series and the heating weights of a
-// bin pair in f32x2, the rounding to counts and the running species and
-// heating sums per bin in bin order.  Gives the same bits as the scalar form.
+// instruction: the optical depths, the series, the absorbed counts and the
+// species and heating sums of a bin pair in f32x2; the rounding to counts
+// per bin.  Gives the same bits as the scalar form (whose sums run over the
+// even and the odd bins separately, as the two lanes do).
+//
+// The species and heating sums factor the segment's optical depth per
+// species out of the bin sum: the share of species s in bin j is
+// q_j t_s sigma_s,j (q_j the absorbed count over tau_j, t_s = l n_s), so the
+// cell's He I share is t_HeI sum_j q_j sigma_HeI,j and its heating
+// sum_s t_s sum_j q_j (sigma w)_s,j; per bin pair that is one packed fma per
+// sum.
 //
 // THIN: every bin of the cell has tau < 0.5 (known from one bound for the
 // whole cell), so every bin takes the series and A = rint(m (1 - e^-tau))
-// needs no clamp: it is at most 0.4 m + 1/2, below m for m >= 1.
+// needs no clamp: it is at most 0.4 m + 1/2, below m for m >= 1, so a bin
+// that held photons still holds some and the packet's liveness is unchanged
+// (left is not recomputed).
 template <int NBT, bool HE, bool HEAT, bool THIN>
 __device__ __forceinline__ void attenuate_bins_x2(const f32x2 tHI2, const f32x2 tHeI2, const f32x2 tHeII2,
                                                   Content<NBT>& c, const BinTables& t,
-                                                  unsigned long long& At, unsigned& left, float& fHeI,
-                                                  float& fHeII, float& fheat) {
+                                                  unsigned long long& At, unsigned& left, f32x2& g1,
+                                                  f32x2& g2, f32x2& h0, f32x2& h1, f32x2& h2) {
+  if (!THIN) left = 0;
 #pragma unroll
   for (int j = 0; j < NBT; j += 2) {
     const f32x2 s0 = f2(t.sigma32[0][j], t.sigma32[0][j + 1]);
-    const f32x2 k0 = f2_mul(tHI2, s0);
-    f32x2 tau = k0, k1 = 0ull, k2 = 0ull;
+    f32x2 tau = f2_mul(tHI2, s0);
+    f32x2 s1 = 0ull, s2 = 0ull;
     if (HE) {
-      const f32x2 s1 = f2(t.sigma32[1][j], t.sigma32[1][j + 1]);
-      const f32x2 s2 = f2(t.sigma32[2][j], t.sigma32[2][j + 1]);
-      k1 = f2_mul(tHeI2, s1);
-      k2 = f2_mul(tHeII2, s2);
-      tau = f2_fma(tHeII2, s2, f2_fma(tHeI2, s1, k0));
+      s1 = f2(t.sigma32[1][j], t.sigma32[1][j + 1]);
+      s2 = f2(t.sigma32[2][j], t.sigma32[2][j + 1]);
+      tau = f2_fma(tHeII2, s2, f2_fma(tHeI2, s1, tau));
     }
     const unsigned m0 = c.m[j], m1 = c.m[j + 1];
     const float N0 = __uint2float_rn(m0), N1 = __uint2float_rn(m1);
-    const f32x2 Nf = f2(N0, N1);
     // (1 - e^-tau)/tau by the same Horner steps as absorbed_over_tau
-    f32x2 p = f2(-1.0f / 40320.0f, -1.0f / 40320.0f);
-    p = f2_fma(p, tau, f2(1.0f / 5040.0f, 1.0f / 5040.0f));
-    p = f2_fma(p, tau, f2(-1.0f / 720.0f, -1.0f / 720.0f));
-    p = f2_fma(p, tau, f2(1.0f / 120.0f, 1.0f / 120.0f));
-    p = f2_fma(p, tau, f2(-1.0f / 24.0f, -1.0f / 24.0f));
-    p = f2_fma(p, tau, f2(1.0f / 6.0f, 1.0f / 6.0f));
-    p = f2_fma(p, tau, f2(-0.5f, -0.5f));
-    p = f2_fma(p, tau, f2(1.0f, 1.0f));
-    const f32x2 q2 = f2_mul(Nf, p);
-    float q0, q1;
-    f2_split(q2, q0, q1);
+    f32x2 p = f2(CRASH_AOT_C5, CRASH_AOT_C5);
+    p = f2_fma(p, tau, f2(CRASH_AOT_C4, CRASH_AOT_C4));
+    p = f2_fma(p, tau, f2(CRASH_AOT_C3, CRASH_AOT_C3));
+    p = f2_fma(p, tau, f2(CRASH_AOT_C2, CRASH_AOT_C2));
+    p = f2_fma(p, tau, f2(CRASH_AOT_C1, CRASH_AOT_C1));
+    p = f2_fma(p, tau, f2(CRASH_AOT_C0, CRASH_AOT_C0));
+    f32x2 q2 = f2_mul(f2(N0, N1), p);
     // a bin with no photons or no optical depth absorbs nothing and adds
-    // nothing below (q k = 0), as when the scalar form skips it
+    // nothing below (q = 0 or sigma = 0), as when the scalar form skips it
     unsigned A0, A1;
     if (THIN) {
       float qt0, qt1;
@@ -251,49 +279,71 @@ __device__ __forceinline__ void attenuate_bins_x2(const f32x2 tHI2, const f32x2 
       A0 = __float2uint_rn(qt0);
       A1 = __float2uint_rn(qt1);
     } else {
-      float tau0, tau1;
+      float tau0, tau1, q0, q1;
       f2_split(tau, tau0, tau1);
+      f2_split(q2, q0, q1);
       A0 = absorb_lane(m0, N0, tau0, q0);
       A1 = absorb_lane(m1, N1, tau1, q1);
+      q2 = f2(q0, q1);
     }
     c.m[j] = m0 - A0;
     c.m[j + 1] = m1 - A1;
     At += A0;
     At += A1;
-    left |= (m0 - A0) | (m1 - A1);
-    float a0, a1, b0, b1;
+    if (!THIN) left |= (m0 - A0) | (m1 - A1);
     if (HE) {
-      f2_split(k1, a0, a1);
-      f2_split(k2, b0, b1);
-      fHeI = fmaf(q0, a0, fHeI);
-      fHeII = fmaf(q0, b0, fHeII);
+      g1 = f2_fma(q2, s1, g1);
+      g2 = f2_fma(q2, s2, g2);
     }
     if (HEAT) {
-      float w0, w1;
+      h0 = f2_fma(q2, f2(t.sw32[0][j], t.sw32[0][j + 1]), h0);
       if (HE) {
-        const f32x2 w = f2_fma(k0, f2(t.wheat32[0][j], t.wheat32[0][j + 1]),
-                               f2_fma(k1, f2(t.wheat32[1][j], t.wheat32[1][j + 1]),
-                                      f2_mul(k2, f2(t.wheat32[2][j], t.wheat32[2][j + 1]))));
-        f2_split(w, w0, w1);
-        fheat = fmaf(q0, w0, fheat);
-      } else {
-        float c0, c1;
-        f2_split(k0, c0, c1);
-        fheat = fmaf(q0 * c0, t.wheat32[0][j], fheat);
-        fheat = fmaf(q1 * c1, t.wheat32[0][j + 1], fheat);
+        h1 = f2_fma(q2, f2(t.sw32[1][j], t.sw32[1][j + 1]), h1);
+        h2 = f2_fma(q2, f2(t.sw32[2][j], t.sw32[2][j + 1]), h2);
       }
-      if (HE) {
-        fHeI = fmaf(q1, a1, fHeI);
-        fHeII = fmaf(q1, b1, fHeII);
-        fheat = fmaf(q1, w1, fheat);
-      }
-    } else if (HE) {
-      fHeI = fmaf(q1, a1, fHeI);
-      fHeII = fmaf(q1, b1, fHeII);
     }
   }
 }
 
+// the sum of the two lanes of a pair
+__device__ __forceinline__ float f2_sum(f32x2 v) {
+  float lo, hi;
+  f2_split(v, lo, hi);
+  return lo + hi;
+}
+
+// The cell's species and heating shares from the per-species bin sums (in
+// the packet's units), scaled to photon quanta and rounded once: He I and
+// He II clamped to the absorbed total, H I taking the rest.
+template <bool HE, bool HEAT>
+__device__ __forceinline__ void cell_shares(unsigned long long At, int e, float tHI, float tHeI, float tHeII,
+                                            float G1, float G2, float H0, float H1, float H2,
+                                            long long& dHI, long long& dHeI, long long& dHeII,
+                                            long long& dE) {
+  long long a1 = 0, a2 = 0, h = 0;
+  const long long Au = (long long)(At << e);
+  if (At) {
+    const float unit = __uint_as_float((unsigned)(127 + e) << 23);
+    const float fHeI = HE ? tHeI * G1 : 0.f, fHeII = HE ? tHeII * G2 : 0.f;
+    const float fheat = HEAT ? (HE ? fmaf(tHeII, H2, fmaf(tHeI, H1, tHI * H0)) : tHI * H0) : 0.f;
+    round_shares(Au, fHeI * unit, fHeII * unit, fheat * unit, a1, a2, h);
+    if (!HE) a1 = a2 = 0;
+    if (!HEAT) h = 0;
+    // He shares above the cell's total only by rounding: clamp then (the
+    // clamps change nothing when the two fit)
+    if (HE && (unsigned long long)a1 + (unsigned long long)a2 > (unsigned long long)Au) {
+      a1 = a1 > Au ? Au : a1;
+      a2 = a2 > Au - a1 ? Au - a1 : a2;
+    }
+  }
+  dHeI = a1;
+  dHeII = a2;
+  dHI = Au - a1 - a2;
+  dE = h;
+}
+
+// left: on entry, nonzero if some bin holds photons; on return, the same
+// after the cell
 template <int NBT, bool HE, bool HEAT>
 __device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, float4 ab, Content<NBT>& c,
                                                        const BinTables& t, long long& dHI,
@@ -304,43 +354,26 @@ __device__ __forceinline__ long long cell_attenuate_x2(float seg, float dl, floa
   const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
   const f32x2 tHI2 = f2(tHI, tHI), tHeI2 = f2(tHeI, tHeI), tHeII2 = f2(tHeII, tHeII);
   unsigned long long At = 0;
-  left = 0;
-  float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
+  f32x2 g1 = 0ull, g2 = 0ull, h0 = 0ull, h1 = 0ull, h2 = 0ull;
   // the optical depth of every bin is at most this bound, computed with the
   // largest cross sections in the same operation order (rounding is monotone)
   const float k0max = tHI * t.sigma32_max[0];
   const float tau_max = HE ? fmaf(tHeII, t.sigma32_max[2], fmaf(tHeI, t.sigma32_max[1], k0max)) : k0max;
   if (tau_max < 0.5f)
-    attenuate_bins_x2<NBT, HE, HEAT, true>(tHI2, tHeI2, tHeII2, c, t, At, left, fHeI, fHeII, fheat);
+    attenuate_bins_x2<NBT, HE, HEAT, true>(tHI2, tHeI2, tHeII2, c, t, At, left, g1, g2, h0, h1, h2);
   else
-    attenuate_bins_x2<NBT, HE, HEAT, false>(tHI2, tHeI2, tHeII2, c, t, At, left, fHeI, fHeII, fheat);
-  long long a1 = 0, a2 = 0, h = 0;
-  const long long Au = (long long)(At << c.e);
-  if (At) {
-    const float unit = __uint_as_float((unsigned)(127 + c.e) << 23);
-    if (HE) {
-      a1 = float_to_ll(fHeI * unit);
-      a2 = float_to_ll(fHeII * unit);
-      // He shares above the cell's total only by rounding: clamp then (the
-      // clamps change nothing when the two fit)
-      if ((unsigned long long)a1 + (unsigned long long)a2 > (unsigned long long)Au) {
-        a1 = a1 > Au ? Au : a1;
-        a2 = a2 > Au - a1 ? Au - a1 : a2;
-      }
-    }
-    if (HEAT) h = float_to_ll(fheat * unit);
-  }
-  dHeI = a1;
-  dHeII = a2;
-  dHI = Au - a1 - a2;
-  dE = h;
-  return Au;
+    attenuate_bins_x2<NBT, HE, HEAT, false>(tHI2, tHeI2, tHeII2, c, t, At, left, g1, g2, h0, h1, h2);
+  cell_shares<HE, HEAT>(At, c.e, tHI, tHeI, tHeII, f2_sum(g1), f2_sum(g2), f2_sum(h0), f2_sum(h1),
+                        f2_sum(h2), dHI, dHeI, dHeII, dE);
+  return (long long)(At << c.e);
 }
 
 // Attenuation and deposition in one crossed cell (Sec. 2, Eq. 1) for a
 // segment of seg cells: updates the packet's bins and returns the absorbed
 // total in photon quanta; the species and heating deposits of the cell come
-// back in d* (quanta), left is nonzero while some bin holds photons.
+// back in d* (quanta), left is nonzero while some bin holds photons.  The
+// species and heating sums run over the even and the odd bins separately
+// and are then added, as the two lanes of the packed form do.
 template <int NBT, bool HE, bool HEAT>
 __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 ab, Content<NBT>& c,
                                                     int nb, const BinTables& t, long long& dHI,
@@ -352,56 +385,37 @@ __device__ __forceinline__ long long cell_attenuate(float seg, float dl, float4 
   const float tHI = l * ab.x, tHeI = l * ab.y, tHeII = l * ab.z;
   unsigned long long At = 0;
   left = 0;
-  float fHeI = 0.f, fHeII = 0.f, fheat = 0.f;
+  float g1[2] = {0.f, 0.f}, g2[2] = {0.f, 0.f}, h0[2] = {0.f, 0.f}, h1[2] = {0.f, 0.f}, h2[2] = {0.f, 0.f};
 #pragma unroll
   for (int j = 0; j < (NBT > 0 ? NBT : CRASH_MAX_BINS); ++j) {
     if (NBT == 0 && j >= nb) break;
-    const float k0 = tHI * t.sigma32[0][j];
-    float tau = k0, k1 = 0.f, k2 = 0.f;
-    if (HE) {
-      k1 = tHeI * t.sigma32[1][j];
-      k2 = tHeII * t.sigma32[2][j];
-      tau = fmaf(tHeII, t.sigma32[2][j], fmaf(tHeI, t.sigma32[1][j], k0));
-    }
+    float tau = tHI * t.sigma32[0][j];
+    if (HE) tau = fmaf(tHeII, t.sigma32[2][j], fmaf(tHeI, t.sigma32[1][j], tau));
     unsigned mj = c.m[j];
-    if (tau > 0.f && mj > 0u) {
+    if (mj > 0u) {
       float q;
       const unsigned A = absorb(mj, tau, q);
       mj -= A;
       c.m[j] = mj;
       At += A;
+      const int o = j & 1;
       if (HE) {
-        fHeI = fmaf(q, k1, fHeI);
-        fHeII = fmaf(q, k2, fHeII);
+        g1[o] = fmaf(q, t.sigma32[1][j], g1[o]);
+        g2[o] = fmaf(q, t.sigma32[2][j], g2[o]);
       }
       if (HEAT) {
-        if (HE)
-          fheat = fmaf(q, fmaf(k0, t.wheat32[0][j], fmaf(k1, t.wheat32[1][j], k2 * t.wheat32[2][j])), fheat);
-        else
-          fheat = fmaf(q * k0, t.wheat32[0][j], fheat);
+        h0[o] = fmaf(q, t.sw32[0][j], h0[o]);
+        if (HE) {
+          h1[o] = fmaf(q, t.sw32[1][j], h1[o]);
+          h2[o] = fmaf(q, t.sw32[2][j], h2[o]);
+        }
       }
     }
     left |= mj;
   }
-  // species split and heating rounded once per cell in photon quanta (the
-  // FP32 sums are in the packet's units; scaling by 2^e is exact)
-  long long a1 = 0, a2 = 0, h = 0;
-  const long long Au = (long long)(At << c.e);
-  if (At) {
-    const float unit = __uint_as_float((unsigned)(127 + c.e) << 23);
-    if (HE) {
-      a1 = float_to_ll(fHeI * unit);
-      a1 = a1 > Au ? Au : a1;
-      a2 = float_to_ll(fHeII * unit);
-      a2 = a2 > Au - a1 ? Au - a1 : a2;
-    }
-    if (HEAT) h = float_to_ll(fheat * unit);
-  }
-  dHeI = a1;
-  dHeII = a2;
-  dHI = Au - a1 - a2;
-  dE = h;
-  return Au;
+  cell_shares<HE, HEAT>(At, c.e, tHI, tHeI, tHeII, g1[0] + g1[1], g2[0] + g2[1], h0[0] + h0[1],
+                        h1[0] + h1[1], h2[0] + h2[1], dHI, dHeI, dHeII, dE);
+  return (long long)(At << c.e);
 }
 
 // Where a walk reads absorbers and adds deposits: the grid in global memory
@@ -490,9 +504,10 @@ struct TileCells {
 // also stops (alive) when it steps out of the box [tx0,tx0+ex) x ... .
 // With PER, a box flagged periodic wraps the walk at its faces and ends it
 // (ESCAPED) once the path trem (cells, the rest of c dt) is used up, the
-// last segment cut there (Sec. 2 periodic boxes).
+// last segment cut there (Sec. 2 periodic boxes).  The photons the walk
+// absorbed are counted once at its end, as the drop of the packet's content.
 template <int NBT, bool HE, bool HEAT, bool TILE, bool PER, class Cells>
-__device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float& tMy, float& tMz,
+__device__ __forceinline__ int walk_steps(int& ix, int& iy, int& iz, float& tMx, float& tMy, float& tMz,
                                     const float dx, const float dy, const float dz, Content<NBT>& N,
                                     const BoxMeta* M, const Cells& cells, const BinTables& t,
                                     const int nb, const int max_iter, Tally& tl, int tx0 = 0,
@@ -507,6 +522,10 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
   const float dl = M->dlf;
   const bool heat_box = HEAT && !M->isothermal;
   if (max_iter <= 0) return ALIVE;
+  unsigned left = 0;
+#pragma unroll
+  for (int j = 0; j < (NBT > 0 ? NBT : CRASH_MAX_BINS); ++j)
+    if (NBT > 0 || j < nb) left |= N.m[j];
   // current segment
   float seg = fminf(tMx, fminf(tMy, tMz));
   int ax = (tMx <= tMy && tMx <= tMz) ? 0 : (tMy <= tMz ? 1 : 2);
@@ -551,13 +570,9 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
     // attenuate and deposit in the current cell
     if (seg > 0.f) {
       long long dHI, dHeI, dHeII, dE;
-      unsigned left;
       const long long Atot = cell_attenuate<NBT, HE, HEAT>(seg, dl, ab, N, nb, t, dHI, dHeI, dHeII,
                                                            dE, left);
-      if (Atot) {
-        cells.add(cell, dHI, dHeI, dHeII, heat_box ? dE : 0ll);
-        tl.absorbed += (unsigned long long)Atot;
-      }
+      if (Atot) cells.add(cell, dHI, dHeI, dHeII, heat_box ? dE : 0ll);
       tl.crossings += 1;
       if (left == 0) return ABSORBED;
     }
@@ -570,6 +585,20 @@ __device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float
     cell = cell_n;
     ab = ab_n;
   }
+}
+
+template <int NBT, bool HE, bool HEAT, bool TILE, bool PER, class Cells>
+__device__ __forceinline__ int walk(int& ix, int& iy, int& iz, float& tMx, float& tMy, float& tMz,
+                                    const float dx, const float dy, const float dz, Content<NBT>& N,
+                                    const BoxMeta* M, const Cells& cells, const BinTables& t,
+                                    const int nb, const int max_iter, Tally& tl, int tx0 = 0,
+                                    int ty0 = 0, int tz0 = 0, int ex = 0, int ey = 0, int ez = 0,
+                                    float* trem = nullptr) {
+  tl.absorbed += N.total(nb);
+  const int r = walk_steps<NBT, HE, HEAT, TILE, PER>(ix, iy, iz, tMx, tMy, tMz, dx, dy, dz, N, M, cells, t,
+                                                     nb, max_iter, tl, tx0, ty0, tz0, ex, ey, ez, trem);
+  tl.absorbed -= N.total(nb);
+  return r;
 }
 
 // the walk over the grid in global memory
