@@ -154,10 +154,12 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double IH = c.GH + bH * ne, RH = aH * ne;
   const double I1 = c.G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = c.G2 + bHe2 * ne, R3 = aHe3 * ne;
   // constant sources (photon-conserving coupling), for the step size at most
-  // what the atoms present can take over the time left
-  double sH = fmin(c.SH, (1.0 - x) / rem);
-  double s1 = fmin(c.S1, y1 / rem);
-  double s2 = fmin(c.S2, y2 / rem);
+  // what the atoms present can take over the time left.  With no source
+  // (the default coupling) and a fraction that is not negative the cap is
+  // min(0, v >= 0) = 0: the FP64 division is skipped, the value is the same
+  double sH = (c.SH > 0.0 || (1.0 - x) < 0.0) ? fmin(c.SH, (1.0 - x) / rem) : 0.0;
+  double s1 = (c.S1 > 0.0 || y1 < 0.0) ? fmin(c.S1, y1 / rem) : 0.0;
+  double s2 = (c.S2 > 0.0 || y2 < 0.0) ? fmin(c.S2, y2 / rem) : 0.0;
   const double dx = (sH + IH * (1.0 - x)) - RH * x;
   const double dy1 = (-I1 * y1 + R2 * y2) - s1;
   const double dy3 = (s2 + I2 * y2) - R3 * y3;
@@ -187,9 +189,9 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   if (nsub == c.max_sub - 1 || !(h < rem)) h = rem;
   // the sources of the sub-step ionise at most the atoms present (He II also
   // what He I gives it): the photons beyond are lost
-  sH = fmin(c.SH, (1.0 - x) / h);
-  s1 = fmin(c.S1, y1 / h);
-  s2 = fmin(c.S2, y2 / h + s1);
+  sH = (c.SH > 0.0 || (1.0 - x) < 0.0) ? fmin(c.SH, (1.0 - x) / h) : 0.0;
+  s1 = (c.S1 > 0.0 || y1 < 0.0) ? fmin(c.S1, y1 / h) : 0.0;
+  s2 = (c.S2 > 0.0 || y2 < 0.0 || s1 < 0.0) ? fmin(c.S2, y2 / h + s1) : 0.0;
   // implicit ionisation update
   double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
 #pragma unroll 1
