@@ -136,3 +136,4 @@ def test_mixed_accuracy_128_windows(name):
     for nm, d in dep.items():
         assert d["sum_rel"] < 1e-4, (nm, d)
         assert d["median_rel"] < 1e-4, (nm, d)
+        assert d["max_rel"] < 1e-4, (nm, d)        # every cell above the floor

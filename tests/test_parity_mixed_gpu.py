@@ -172,8 +172,12 @@ def test_mixed_full_size_512_window_against_oracle():
     from test_mixed_accuracy_gpu import _deposit_stats, _report
     dep = _deposit_stats(g, o)
     _report(w.name + "_window", {"packet_ids": [0, 2], "deposits": dep})
+    # Per cell, above the floor: the FP32 walk can hand a corner-clipping
+    # segment of a few 1e-5 cells to a neighbouring cell; near the floor, in
+    # cells crossed by a handful of packets, that shows at about 1e-3.
     for nm, d in dep.items():
         assert d["sum_rel"] < 1e-4 and d["median_rel"] < 1e-4, (nm, d)
+        assert d["p99_rel"] < 5e-4 and d["max_rel"] < 2e-3, (nm, d)
 
 
 def test_batch_64_recipe_graph_equals_separate_boxes():
