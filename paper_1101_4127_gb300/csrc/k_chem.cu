@@ -182,7 +182,8 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
     const double L = cooling_rate(r, c.mask, ne, nHI, nHII, c.nHe * y1, c.nHe * y2, c.nHe * y3) +
                      c.ccomp * ne * (T - c.Tcmb);
     const double dne = c.nH * dx + c.nHe * (dy2 + 2.0 * dy3);
-    const double dT = ((heat - L) / (1.5 * kB) - T * dne) / ntot;
+    // (dT is only the step-size estimate: the reciprocal constant's rounding does not matter)
+    const double dT = ((heat - L) * (1.0 / (1.5 * kB)) - T * dne) / ntot;
     const double adT = fabs(dT);
     if (adT * h > c.eps * T) h = c.eps * T / adT;
   }
@@ -197,7 +198,8 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
 #pragma unroll 1
   for (int it = 0; it < 4; ++it) {
     const double ih = c.GH + bH * nen, rh = aH * nen;
-    xn = (x + h * (sH + ih)) / (1.0 + h * (ih + rh));
+    const double xnum = x + h * (sH + ih), xden = 1.0 + h * (ih + rh);
+    if (!he) xn = xnum / xden;
     if (he) {
       const double i1 = c.G1 + bHe1 * nen, r2 = aHe2 * nen;
       const double i2 = c.G2 + bHe2 * nen, r3 = aHe3 * nen;
@@ -211,7 +213,12 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
       const double c1 = a12 * inv11, d1 = b1 * inv11;
       const double inv2 = 1.0 / (a22 - a21 * c1);
       const double c2 = a23 * inv2, d2 = (b2 - a21 * d1) * inv2;
-      y3n = (b3 - a32 * d2) / (a33 - a32 * c2);
+      // the last elimination step and the H update share one division
+      // (both denominators are at least 1)
+      const double den3 = a33 - a32 * c2;
+      const double r = 1.0 / (xden * den3);
+      y3n = ((b3 - a32 * d2) * xden) * r;
+      xn = (xnum * den3) * r;
       y2n = d2 - c2 * y3n;
       y1n = d1 - c1 * y2n;
     }
@@ -225,9 +232,9 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
     y1n = fmax(y1n, 0.0);
     y2n = fmax(y2n, 0.0);
     y3n = fmax(y3n, 0.0);
-    const double s = (y1n + y2n) + y3n;
-    y2n = y2n / s;
-    y3n = y3n / s;
+    const double inv_s = 1.0 / ((y1n + y2n) + y3n);
+    y2n = y2n * inv_s;
+    y3n = y3n * inv_s;
     y1n = (1.0 - y2n) - y3n;
   }
   const double ne2 = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
@@ -236,10 +243,11 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
     const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n) + c.heat_rate;
     const double L = cooling_rate(r, c.mask, ne2, nHI, nHII, c.nHe * y1n, c.nHe * y2n,
                                   c.nHe * y3n);
-    const double L1 = L / T;
     const double Cc = c.ccomp * ne2;
     const double ntot2 = c.nH + c.nHe + ne2;
-    T = (1.5 * kB * ntot * T + h * (heat + Cc * c.Tcmb)) / (1.5 * kB * ntot2 + h * (L1 + Cc));
+    // semi-implicit cooling (linear in the new T): numerator and denominator
+    // of the update taken times T, so that L / T needs no division of its own
+    T = ((1.5 * kB * ntot * T + h * (heat + Cc * c.Tcmb)) * T) / ((1.5 * kB * ntot2 + h * Cc) * T + h * L);
   }
   if (COUNT && c.count_rec && rec) {
     nrec[0] += h * gH * ne2 * (c.nH * xn);
