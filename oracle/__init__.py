@@ -51,7 +51,8 @@ class GridDesc(C.Structure):
                 ("x_HII0", C.c_double), ("x_HeII0", C.c_double), ("x_HeIII0", C.c_double),
                 ("T0", C.c_double), ("isothermal", C.c_int), ("caseB", C.c_int),
                 ("z_compton", C.c_double), ("seed", C.c_uint64), ("f_rec", C.c_double),
-                ("coupling", C.c_int), ("periodic", C.c_int)]
+                ("coupling", C.c_int), ("periodic", C.c_int),
+                ("uv_rate", C.c_double * 3), ("uv_heat_eV", C.c_double * 3)]
 
 
 class ChemCell(C.Structure):
@@ -61,6 +62,8 @@ class ChemCell(C.Structure):
                 ("G_HeII", C.c_double), ("heat_per_ion", C.c_double),
                 ("S_HI", C.c_double), ("S_HeI", C.c_double), ("S_HeII", C.c_double),
                 ("heat_rate", C.c_double),
+                ("U_HI", C.c_double), ("U_HeI", C.c_double), ("U_HeII", C.c_double),
+                ("Ue_HI", C.c_double), ("Ue_HeI", C.c_double), ("Ue_HeII", C.c_double),
                 ("isothermal", C.c_int), ("caseB", C.c_int), ("T_cmb", C.c_double),
                 ("eps", C.c_double), ("max_sub", C.c_int), ("cool_mask", C.c_int),
                 ("count_rec", C.c_int), ("rec", C.c_double * 3)]
@@ -158,7 +161,8 @@ def chem_cell(dt: float, **kw):
     c = ChemCell()
     defaults = dict(nH=1e-3, nHe=0.0, xHII=0.0, xHeII=0.0, xHeIII=0.0, T=1e4, G_HI=0.0,
                     G_HeI=0.0, G_HeII=0.0, heat_per_ion=0.0, S_HI=0.0, S_HeI=0.0, S_HeII=0.0,
-                    heat_rate=0.0, isothermal=0, caseB=1,
+                    heat_rate=0.0, U_HI=0.0, U_HeI=0.0, U_HeII=0.0, Ue_HI=0.0, Ue_HeI=0.0,
+                    Ue_HeII=0.0, isothermal=0, caseB=1,
                     T_cmb=0.0, eps=0.1, max_sub=10000, cool_mask=C_ALL, count_rec=0)
     defaults.update(kw)
     for k, v in defaults.items():
@@ -185,7 +189,7 @@ class OracleGrid:
                  x_HII=None, x_HeII=None, x_HeIII=None, T=None,
                  x_HII0=0.0, x_HeII0=0.0, x_HeIII0=0.0, T0=1e4,
                  isothermal=0, caseB=1, z_compton=-1.0, seed=0, f_rec=0.0, coupling=0,
-                 periodic=0):
+                 periodic=0, uv_rate=(0.0, 0.0, 0.0), uv_heat_eV=(0.0, 0.0, 0.0)):
         self.L = lib()
         self.shape = (nz, ny, nx)
         self.ncell = nx * ny * nz
@@ -212,6 +216,9 @@ class OracleGrid:
         d.isothermal, d.caseB, d.z_compton, d.seed = isothermal, caseB, z_compton, seed
         d.f_rec = f_rec
         d.coupling, d.periodic = coupling, periodic
+        for k in range(3):
+            d.uv_rate[k] = float(uv_rate[k])
+            d.uv_heat_eV[k] = float(uv_heat_eV[k])
         self.ctx = self.L.oracle_init_grid(C.byref(d))
         if not self.ctx:
             raise RuntimeError("oracle_init_grid failed")
@@ -224,7 +231,9 @@ class OracleGrid:
                 x_HeIII0=box.x_HeIII0, T0=box.T0, isothermal=box.isothermal,
                 caseB=box.caseB, z_compton=box.z_compton, seed=box.seed,
                 f_rec=getattr(box, "f_rec", 0.0), coupling=getattr(box, "coupling", 0),
-                periodic=getattr(box, "periodic", 0))
+                periodic=getattr(box, "periodic", 0),
+                uv_rate=getattr(box, "uv_rate", (0.0, 0.0, 0.0)),
+                uv_heat_eV=getattr(box, "uv_heat_eV", (0.0, 0.0, 0.0)))
         g.add_sources(box.src_pos, box.src_ndot, box.bin_eV, box.bin_frac)
         return g
 

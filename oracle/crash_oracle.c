@@ -58,6 +58,7 @@ struct or_ctx {
   double f_rec;                               /* > 0: diffuse recombination field */
   int coupling;                               /* 1: photon-conserving chemistry coupling */
   int periodic;                               /* 1: periodic box, light-travel stop */
+  double uv_rate[3], uv_heat[3];              /* uniform background: s^-1 per atom, erg */
   double path_limit;                          /* periodic: c dt / dl of this step (cells) */
   uint32_t chem_stride;                       /* timing sample of the per-cell update */
   double dep_scale;
@@ -234,6 +235,15 @@ or_ctx* oracle_init_grid(const or_grid_desc* d) {
   c->f_rec = d->f_rec > 0 ? d->f_rec : 0.0;
   c->coupling = d->coupling ? 1 : 0;
   c->periodic = d->periodic ? 1 : 0;
+  for (int s = 0; s < 3; ++s) {
+    if (!(d->uv_rate[s] >= 0.0) || !isfinite(d->uv_rate[s]) || !(d->uv_heat_eV[s] >= 0.0) ||
+        !isfinite(d->uv_heat_eV[s])) {
+      free(c);
+      return NULL;
+    }
+    c->uv_rate[s] = d->uv_rate[s];
+    c->uv_heat[s] = d->uv_heat_eV[s] * EV;
+  }
   c->path_limit = INFINITY;
   c->chem_stride = 1;
   c->dep_scale = 1.0;
@@ -557,8 +567,10 @@ int or_chem_cell(or_chem_t* c, double dt) {
     double y1 = (1.0 - y2) - y3;
     double ne = nH * x + nHe * (y2 + 2.0 * y3);
     /* derivatives at the start of the sub-step */
-    double IH = c->G_HI + bH * ne, RH = aH * ne;
-    double I1 = c->G_HeI + bHe1 * ne, R2 = aHe2 * ne, I2 = c->G_HeII + bHe2 * ne, R3 = aHe3 * ne;
+    /* photo-ionisation by the deposits and by the uniform background */
+    const double GH = c->G_HI + c->U_HI, G1 = c->G_HeI + c->U_HeI, G2 = c->G_HeII + c->U_HeII;
+    double IH = GH + bH * ne, RH = aH * ne;
+    double I1 = G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = G2 + bHe2 * ne, R3 = aHe3 * ne;
     /* constant-count photo-ionisation sources (photon-conserving coupling),
        for the step size at most what the atoms present can take over the
        time left (a used-up species does not shorten the sub-steps) */
@@ -582,7 +594,9 @@ int or_chem_cell(or_chem_t* c, double dt) {
     if (!c->isothermal) {
       double nHI = nH * (1.0 - x), nHII = nH * x;
       double heat = c->heat_per_ion * (c->G_HI * nHI + c->G_HeI * nHe * y1 + c->G_HeII * nHe * y2) +
-                    c->heat_rate;
+                    c->heat_rate +
+                    ((c->U_HI * c->Ue_HI) * nHI + (c->U_HeI * c->Ue_HeI) * (nHe * y1) +
+                     (c->U_HeII * c->Ue_HeII) * (nHe * y2));
       double L = cooling(r, mask, ne, nHI, nHII, nHe * y1, nHe * y2, nHe * y3) +
                  ccomp * ne * (T - c->T_cmb);
       double dne = nH * dx + nHe * (dy2 + 2.0 * dy3);
@@ -599,11 +613,11 @@ int or_chem_cell(or_chem_t* c, double dt) {
     /* backward Euler with n_e from the end of the sub-step */
     double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
     for (int it = 0; it < 4; ++it) {
-      double IHn = c->G_HI + bH * nen, RHn = aH * nen;
+      double IHn = GH + bH * nen, RHn = aH * nen;
       xn = (x + h * (sH + IHn)) / (1.0 + h * (IHn + RHn));
       if (nHe > 0) {
-        double i1 = c->G_HeI + bHe1 * nen, r2 = aHe2 * nen;
-        double i2 = c->G_HeII + bHe2 * nen, r3 = aHe3 * nen;
+        double i1 = G1 + bHe1 * nen, r2 = aHe2 * nen;
+        double i2 = G2 + bHe2 * nen, r3 = aHe3 * nen;
         double a11 = 1.0 + h * i1, a12 = -h * r2;
         double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
         double a32 = -h * i2, a33 = 1.0 + h * r3;
@@ -637,7 +651,9 @@ int or_chem_cell(or_chem_t* c, double dt) {
     if (!c->isothermal) {
       double nHI = nH * (1.0 - xn), nHII = nH * xn;
       double heat = c->heat_per_ion * (c->G_HI * nHI + c->G_HeI * nHe * y1n + c->G_HeII * nHe * y2n) +
-                    c->heat_rate;
+                    c->heat_rate +
+                    ((c->U_HI * c->Ue_HI) * nHI + (c->U_HeI * c->Ue_HeI) * (nHe * y1n) +
+                     (c->U_HeII * c->Ue_HeII) * (nHe * y2n));
       double L = cooling(r, mask, nen2, nHI, nHII, nHe * y1n, nHe * y2n, nHe * y3n);
       double L1 = L / T;
       double C = ccomp * nen2;
@@ -685,6 +701,9 @@ static void or_step_chemistry(or_ctx* c, double dt, int E) {
     const double dHeII = (double)c->dHeII[i] * c->dep_scale, dE = (double)c->dE[i] * c->dep_scale;
     ch.S_HI = ch.S_HeI = ch.S_HeII = 0.0;
     ch.heat_rate = 0.0;
+    /* the uniform background acts in every cell, whatever the deposits */
+    ch.U_HI = c->uv_rate[0]; ch.U_HeI = c->uv_rate[1]; ch.U_HeII = c->uv_rate[2];
+    ch.Ue_HI = c->uv_heat[0]; ch.Ue_HeI = c->uv_heat[1]; ch.Ue_HeII = c->uv_heat[2];
     if (!c->coupling) {
       /* photo-ionisation rate per absorber frozen at the start of the step */
       double NHI = c->aHI[i] * V, NHeI = c->aHeI[i] * V, NHeII = c->aHeII[i] * V;

@@ -51,6 +51,11 @@ typedef struct {
   int periodic;                  /* 1: periodic box (Sec. 2): a packet leaving a face
                                     re-enters at the opposite one and stops after the
                                     distance light travels in the step, c dt */
+  double uv_rate[3];             /* uniform background (Sec. 2 "background field", a
+                                    reading): photo-ionisations per atom of H I, He I,
+                                    He II and s, the same in every cell and not
+                                    attenuated; 0 = off */
+  double uv_heat_eV[3];          /* energy each such photo-ionisation leaves as heat, eV */
 } or_grid_desc;
 
 typedef struct or_ctx or_ctx;
@@ -105,6 +110,9 @@ typedef struct {
                                        s^-1 (photon-conserving coupling); in a sub-step each
                                        ionises at most the atoms of its species present */
   double heat_rate;                 /* constant photo-heating, erg cm^-3 s^-1 */
+  double U_HI, U_HeI, U_HeII;       /* uniform background photo-ionisation rate per atom of
+                                       the species, s^-1 (added to G_*) */
+  double Ue_HI, Ue_HeI, Ue_HeII;    /* heat per such photo-ionisation, erg */
   int isothermal, caseB;
   double T_cmb;                     /* <= 0: Compton off */
   double eps;                       /* relative change allowed per sub-step */

@@ -144,6 +144,8 @@ class Box:
     f_rec: float = 0.0            # > 0: diffuse recombination field with this threshold
     coupling: int = 0             # 1: photon-conserving transport -> chemistry coupling
     periodic: int = 0             # 1: periodic box, packets stop after the light-travel distance
+    uv_rate: tuple = (0.0, 0.0, 0.0)     # uniform background photo-ionisations per atom (H I, He I, He II), s^-1
+    uv_heat_eV: tuple = (0.0, 0.0, 0.0)  # heat left by each such photo-ionisation, eV
 
     @property
     def n_src(self) -> int:
