@@ -112,6 +112,13 @@ typedef struct {
                                 what it still holds then is counted as escaped.  Periodic
                                 boxes trace every packet to its end in its own thread (the
                                 mixed form's wavefront keeps no path budget). */
+  double uv_rate[3];         /* uniform background (Sec. 2 "background field"; the paper
+                                gives neither its intensity nor its spectrum, so it is
+                                taken as given rates): photo-ionisations per atom of H I,
+                                He I and He II and second, the same in every cell, not
+                                attenuated, added to the rates from the deposits in the
+                                per-cell update (>= 0, finite; 0 = off, the default) */
+  double uv_heat_eV[3];      /* heat each such photo-ionisation leaves in the gas, eV (>= 0) */
 } crash_grid_desc;
 
 /* Run options (crash_default_opts fills the defaults). */

@@ -192,6 +192,10 @@ static crash_status validate_desc(const crash_grid_desc& d, int i) {
   if (!(d.f_rec >= 0 && d.f_rec <= 1)) return set_err(c, CRASH_ERR_ARG, "f_rec must be in [0, 1]");
   if (d.coupling != 0 && d.coupling != 1) return set_err(c, CRASH_ERR_ARG, "coupling must be 0 or 1");
   if (d.periodic != 0 && d.periodic != 1) return set_err(c, CRASH_ERR_ARG, "periodic must be 0 or 1");
+  for (int s = 0; s < 3; ++s)
+    if (!(d.uv_rate[s] >= 0) || !std::isfinite(d.uv_rate[s]) || !(d.uv_heat_eV[s] >= 0) ||
+        !std::isfinite(d.uv_heat_eV[s]))
+      return set_err(c, CRASH_ERR_ARG, "uv_rate and uv_heat_eV must be finite and >= 0");
   return CRASH_OK;
 }
 
@@ -265,6 +269,10 @@ extern "C" crash_status crash_init_batch(int n_boxes, const crash_grid_desc* des
     m.f_rec = d.f_rec;
     m.coupling = d.coupling;
     m.periodic = d.periodic;
+    for (int s = 0; s < 3; ++s) {
+      m.uv[s] = d.uv_rate[s];
+      m.uve[s] = d.uv_heat_eV[s];
+    }
     c->any_rec |= d.f_rec > 0;
     c->any_periodic |= d.periodic != 0;
     off += m.ncell;

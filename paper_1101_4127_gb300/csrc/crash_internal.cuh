@@ -54,6 +54,8 @@ struct BoxMeta {
   int coupling;            // 1: photon-conserving transport -> chemistry coupling
   int periodic;            // 1: periodic box, walks end after c dt
   float path_cells32;      // periodic: c dt / dl of this step in FP32 (mixed form)
+  double uv[3];            // uniform background photo-ionisations per atom (s^-1): H I, He I, He II
+  double uve[3];           // heat per such photo-ionisation (eV)
 };
 
 // speed of light (cm/s): the periodic box's light-travel distance per step

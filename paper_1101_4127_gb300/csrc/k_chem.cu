@@ -121,6 +121,8 @@ __device__ __forceinline__ double cooling_rate(const Rates& r, int mask, double 
 struct CellIn {
   double nH, nHe, GH, G1, G2, eps_heat, Tcmb, ccomp, eps, V;
   double SH, S1, S2, heat_rate;   // constant sources per atom of the element (s^-1), erg/cm^3/s
+  double uvH, uv1, uv2;           // uniform background photo-ionisations per atom (s^-1)
+  double uveH, uve1, uve2;        // heat per such photo-ionisation (erg)
   int iso, caseB, mask, max_sub, count_rec;
 };
 
@@ -150,9 +152,11 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double bH = coll ? r.bHI : 0.0, bHe1 = coll ? r.bHeI : 0.0, bHe2 = coll ? r.bHeII : 0.0;
   const double y1 = (1.0 - y2) - y3;
   const double ne = c.nH * x + c.nHe * (y2 + 2.0 * y3);
+  // photo-ionisation by the deposits and by the uniform background
+  const double GH = c.GH + c.uvH, G1 = c.G1 + c.uv1, G2 = c.G2 + c.uv2;
   // rates of change at the start of the sub-step (for the step size)
-  const double IH = c.GH + bH * ne, RH = aH * ne;
-  const double I1 = c.G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = c.G2 + bHe2 * ne, R3 = aHe3 * ne;
+  const double IH = GH + bH * ne, RH = aH * ne;
+  const double I1 = G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = G2 + bHe2 * ne, R3 = aHe3 * ne;
   // constant sources (photon-conserving coupling), for the step size at most
   // what the atoms present can take over the time left.  With no source
   // (the default coupling) and a fraction that is not negative the cap is
@@ -178,7 +182,8 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double ntot = c.nH + c.nHe + ne;
   if (!c.iso) {
     const double nHI = c.nH * (1.0 - x), nHII = c.nH * x;
-    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2) + c.heat_rate;
+    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2) + c.heat_rate +
+                        ((c.uvH * c.uveH) * nHI + (c.uv1 * c.uve1) * (c.nHe * y1) + (c.uv2 * c.uve2) * (c.nHe * y2));
     const double L = cooling_rate(r, c.mask, ne, nHI, nHII, c.nHe * y1, c.nHe * y2, c.nHe * y3) +
                      c.ccomp * ne * (T - c.Tcmb);
     const double dne = c.nH * dx + c.nHe * (dy2 + 2.0 * dy3);
@@ -197,12 +202,12 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   double xn = x, y1n = y1, y2n = y2, y3n = y3, nen = ne;
 #pragma unroll 1
   for (int it = 0; it < 4; ++it) {
-    const double ih = c.GH + bH * nen, rh = aH * nen;
+    const double ih = GH + bH * nen, rh = aH * nen;
     const double xnum = x + h * (sH + ih), xden = 1.0 + h * (ih + rh);
     if (!he) xn = xnum / xden;
     if (he) {
-      const double i1 = c.G1 + bHe1 * nen, r2 = aHe2 * nen;
-      const double i2 = c.G2 + bHe2 * nen, r3 = aHe3 * nen;
+      const double i1 = G1 + bHe1 * nen, r2 = aHe2 * nen;
+      const double i2 = G2 + bHe2 * nen, r3 = aHe3 * nen;
       // tridiagonal (I - h Q) y_new = y_old, Thomas elimination
       const double a11 = 1.0 + h * i1, a12 = -h * r2;
       const double a21 = -h * i1, a22 = 1.0 + h * (r2 + i2), a23 = -h * r3;
@@ -240,7 +245,8 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double ne2 = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
   if (!c.iso) {
     const double nHI = c.nH * (1.0 - xn), nHII = c.nH * xn;
-    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n) + c.heat_rate;
+    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n) + c.heat_rate +
+                        ((c.uvH * c.uveH) * nHI + (c.uv1 * c.uve1) * (c.nHe * y1n) + (c.uv2 * c.uve2) * (c.nHe * y2n));
     const double L = cooling_rate(r, c.mask, ne2, nHI, nHII, c.nHe * y1n, c.nHe * y2n,
                                   c.nHe * y3n);
     const double Cc = c.ccomp * ne2;
@@ -302,6 +308,9 @@ __device__ __forceinline__ void load_cell(const StepArgs& a, int64_t i, int b, C
     c.S2 = NHe > 0 ? ((double)dHeII * q) / (a.dt * NHe) : 0.0;
     c.heat_rate = ((double)dE * qE) / (a.dt * V);
   }
+  // the uniform background acts in every cell, whatever the deposits
+  c.uvH = M->uv[0]; c.uv1 = M->uv[1]; c.uv2 = M->uv[2];
+  c.uveH = M->uve[0] * eV; c.uve1 = M->uve[1] * eV; c.uve2 = M->uve[2] * eV;
   c.iso = M->isothermal;
   // the diffuse recombination field replaces on-the-spot absorption: case A
   c.caseB = M->f_rec > 0.0 ? 0 : M->caseB;

@@ -47,7 +47,8 @@ class crash_grid_desc(C.Structure):
                 ("x_HII0", C.c_double), ("x_HeII0", C.c_double), ("x_HeIII0", C.c_double),
                 ("T0", C.c_double), ("isothermal", C.c_int), ("caseB", C.c_int),
                 ("z_compton", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int),
-                ("f_rec", C.c_double), ("coupling", C.c_int), ("periodic", C.c_int)]
+                ("f_rec", C.c_double), ("coupling", C.c_int), ("periodic", C.c_int),
+                ("uv_rate", C.c_double * 3), ("uv_heat_eV", C.c_double * 3)]
 
 
 class crash_run_opts(C.Structure):
@@ -155,6 +156,9 @@ def make_desc(box, precision=CRASH_FP64_PLAIN, keep=None):
     d.f_rec = getattr(box, "f_rec", 0.0)
     d.coupling = getattr(box, "coupling", 0)
     d.periodic = getattr(box, "periodic", 0)
+    for k in range(3):
+        d.uv_rate[k] = float(getattr(box, "uv_rate", (0.0, 0.0, 0.0))[k])
+        d.uv_heat_eV[k] = float(getattr(box, "uv_heat_eV", (0.0, 0.0, 0.0))[k])
     return d
 
 

@@ -33,16 +33,17 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_struct_layouts_match_header(tmp_path):
     probe = tmp_path / "probe.c"
     probe.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crash.h"\n'
-                     'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(crash_grid_desc),'
+                     'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(crash_grid_desc),'
                      ' sizeof(crash_run_opts), offsetof(crash_grid_desc, f_rec),'
                      ' offsetof(crash_run_opts, sort_curve), offsetof(crash_grid_desc, periodic),'
-                     ' offsetof(crash_run_opts, chunk_packets));return 0;}\n')
+                     ' offsetof(crash_run_opts, chunk_packets), offsetof(crash_grid_desc, uv_heat_eV));return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HDR), str(probe), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [C.sizeof(native.crash_grid_desc), C.sizeof(native.crash_run_opts),
                    native.crash_grid_desc.f_rec.offset, native.crash_run_opts.sort_curve.offset,
-                   native.crash_grid_desc.periodic.offset, native.crash_run_opts.chunk_packets.offset]
+                   native.crash_grid_desc.periodic.offset, native.crash_run_opts.chunk_packets.offset,
+                   native.crash_grid_desc.uv_heat_eV.offset]
 
 
 def test_argument_errors_are_status_codes():
@@ -68,6 +69,11 @@ def test_argument_errors_are_status_codes():
     d.coupling, d.periodic = 0, 3
     assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
     d.periodic = 0
+    d.uv_rate[1] = -1e-13             # a background rate is >= 0
+    assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
+    d.uv_rate[1], d.uv_heat_eV[2] = 0.0, float("inf")
+    assert L.crash_init_grid(C.byref(d), C.byref(ctx)) == native.CRASH_ERR_ARG
+    d.uv_heat_eV[2] = 0.0
     assert L.crash_step(None, 1.0, 1) == native.CRASH_ERR_ARG
     assert L.crash_chemistry(None, 1.0) == native.CRASH_ERR_ARG
     p = C.c_void_p()
