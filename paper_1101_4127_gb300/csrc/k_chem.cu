@@ -119,10 +119,12 @@ __device__ __forceinline__ double cooling_rate(const Rates& r, int mask, double 
 }
 
 struct CellIn {
-  double nH, nHe, GH, G1, G2, eps_heat, Tcmb, ccomp, eps, V;
+  // GH, G1, G2: photo-ionisation rate per absorber, from the deposits plus
+  // the uniform background; WH, W1, W2: photo-heating per absorber (erg/s),
+  // the deposits' mean excess energy times their rate plus the background's
+  // heat per ionisation times its rate
+  double nH, nHe, GH, G1, G2, WH, W1, W2, Tcmb, ccomp, eps, V;
   double SH, S1, S2, heat_rate;   // constant sources per atom of the element (s^-1), erg/cm^3/s
-  double uvH, uv1, uv2;           // uniform background photo-ionisations per atom (s^-1)
-  double uveH, uve1, uve2;        // heat per such photo-ionisation (erg)
   int iso, caseB, mask, max_sub, count_rec;
 };
 
@@ -152,8 +154,7 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double bH = coll ? r.bHI : 0.0, bHe1 = coll ? r.bHeI : 0.0, bHe2 = coll ? r.bHeII : 0.0;
   const double y1 = (1.0 - y2) - y3;
   const double ne = c.nH * x + c.nHe * (y2 + 2.0 * y3);
-  // photo-ionisation by the deposits and by the uniform background
-  const double GH = c.GH + c.uvH, G1 = c.G1 + c.uv1, G2 = c.G2 + c.uv2;
+  const double GH = c.GH, G1 = c.G1, G2 = c.G2;
   // rates of change at the start of the sub-step (for the step size)
   const double IH = GH + bH * ne, RH = aH * ne;
   const double I1 = G1 + bHe1 * ne, R2 = aHe2 * ne, I2 = G2 + bHe2 * ne, R3 = aHe3 * ne;
@@ -182,8 +183,7 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double ntot = c.nH + c.nHe + ne;
   if (!c.iso) {
     const double nHI = c.nH * (1.0 - x), nHII = c.nH * x;
-    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1 + c.G2 * c.nHe * y2) + c.heat_rate +
-                        ((c.uvH * c.uveH) * nHI + (c.uv1 * c.uve1) * (c.nHe * y1) + (c.uv2 * c.uve2) * (c.nHe * y2));
+    const double heat = (c.WH * nHI + c.W1 * (c.nHe * y1) + c.W2 * (c.nHe * y2)) + c.heat_rate;
     const double L = cooling_rate(r, c.mask, ne, nHI, nHII, c.nHe * y1, c.nHe * y2, c.nHe * y3) +
                      c.ccomp * ne * (T - c.Tcmb);
     const double dne = c.nH * dx + c.nHe * (dy2 + 2.0 * dy3);
@@ -245,8 +245,7 @@ __device__ __forceinline__ void substep(const CellIn& c, double& x, double& y2, 
   const double ne2 = c.nH * xn + c.nHe * (y2n + 2.0 * y3n);
   if (!c.iso) {
     const double nHI = c.nH * (1.0 - xn), nHII = c.nH * xn;
-    const double heat = c.eps_heat * (c.GH * nHI + c.G1 * c.nHe * y1n + c.G2 * c.nHe * y2n) + c.heat_rate +
-                        ((c.uvH * c.uveH) * nHI + (c.uv1 * c.uve1) * (c.nHe * y1n) + (c.uv2 * c.uve2) * (c.nHe * y2n));
+    const double heat = (c.WH * nHI + c.W1 * (c.nHe * y1n) + c.W2 * (c.nHe * y2n)) + c.heat_rate;
     const double L = cooling_rate(r, c.mask, ne2, nHI, nHII, c.nHe * y1n, c.nHe * y2n,
                                   c.nHe * y3n);
     const double Cc = c.ccomp * ne2;
@@ -296,21 +295,28 @@ __device__ __forceinline__ void load_cell(const StepArgs& a, int64_t i, int b, C
     c.G1 = NHeI > 0 ? ((double)dHeI * q) / (a.dt * NHeI) : 0.0;
     c.G2 = NHeII > 0 ? ((double)dHeII * q) / (a.dt * NHeII) : 0.0;
     const long long nabs = (dHI + dHeI) + dHeII;
-    c.eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
+    const double eps_heat = nabs > 0 ? ((double)dE * qE) / ((double)nabs * q) : 0.0;
+    c.WH = eps_heat * c.GH;
+    c.W1 = eps_heat * c.G1;
+    c.W2 = eps_heat * c.G2;
   } else {
     // photon-conserving: one ionisation per absorbed photon at a constant
     // rate per atom of the element, heating at the deposited rate
     const double NH = c.nH * V, NHe = c.nHe * V;
     c.GH = c.G1 = c.G2 = 0.0;
-    c.eps_heat = 0.0;
+    c.WH = c.W1 = c.W2 = 0.0;
     c.SH = NH > 0 ? ((double)dHI * q) / (a.dt * NH) : 0.0;
     c.S1 = NHe > 0 ? ((double)dHeI * q) / (a.dt * NHe) : 0.0;
     c.S2 = NHe > 0 ? ((double)dHeII * q) / (a.dt * NHe) : 0.0;
     c.heat_rate = ((double)dE * qE) / (a.dt * V);
   }
   // the uniform background acts in every cell, whatever the deposits
-  c.uvH = M->uv[0]; c.uv1 = M->uv[1]; c.uv2 = M->uv[2];
-  c.uveH = M->uve[0] * eV; c.uve1 = M->uve[1] * eV; c.uve2 = M->uve[2] * eV;
+  c.GH += M->uv[0];
+  c.G1 += M->uv[1];
+  c.G2 += M->uv[2];
+  c.WH += M->uv[0] * (M->uve[0] * eV);
+  c.W1 += M->uv[1] * (M->uve[1] * eV);
+  c.W2 += M->uv[2] * (M->uve[2] * eV);
   c.iso = M->isothermal;
   // the diffuse recombination field replaces on-the-spot absorption: case A
   c.caseB = M->f_rec > 0.0 ? 0 : M->caseB;
