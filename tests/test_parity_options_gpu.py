@@ -260,3 +260,24 @@ def test_uniform_background_mixed_against_oracle():
     for nm in NAMES:
         assert err[nm]["max_rel_where_ge_0.0001"] < FIELD_TOL, (nm, err[nm])
         assert err[nm]["p99_rel"] < FIELD_TOL, (nm, err[nm])
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_dark_sources_under_the_background_alone(precision):
+    """Degenerate step: every source emits nothing (the photon quantum falls
+    back to 2^0), so every deposit is zero and the budget holds no photons;
+    the background alone updates the cells, as in the oracle."""
+    box = dataclasses.replace(_uv_box(451), src_ndot=np.zeros(2))
+    P = 2 * 512
+    dt = 0.2 * inputs.MYR_S
+    g, o = _pair(box, precision)
+    for _ in range(2):
+        g.step(dt, P)
+        o.step(dt, P)
+    for f, _ in DEP_FIELDS:
+        assert not g.read(f).any(), f
+    b = g.read(native.F_BUDGET)
+    assert b[0] == b[1] == b[2] == 0 and b[4] == P
+    tol = 1e-9 if precision == FP64 else FIELD_TOL
+    for fg, fo in STATE_FIELDS:
+        assert max_rel(g.read(fg), o.read(fo), floor=1e-6) < tol, fg
