@@ -62,7 +62,21 @@ struct WFArgs {
   int tile;                  // keys of 16^3-cell tiles (tile passes) instead of 8^3 buckets
   int curve;                 // 0: Morton order of the buckets, 1: Hilbert order
   int64_t cap;
+  unsigned* work;            // pass kernels: counter of the queue positions handed out
+  unsigned* work_next;       // the next pass's counter, cleared by this pass
 };
+
+// Blocks of a pass take the next blockDim.x packets of the queue as they
+// finish: walks differ in length, and a fixed grid stride leaves blocks idle
+// at the end of the pass while a few finish theirs.  Returns the first
+// position of the block's packets (>= n: the queue is exhausted).
+__device__ __forceinline__ int64_t next_block_packets(unsigned* work) {
+  __shared__ unsigned s_base;
+  __syncthreads();                   // every thread has read the previous s_base
+  if (threadIdx.x == 0) s_base = atomicAdd(work, (unsigned)blockDim.x);
+  __syncthreads();
+  return (int64_t)s_base;
+}
 
 struct Tally {
   unsigned long long emitted, absorbed, escaped;
@@ -887,9 +901,12 @@ template <int NBT, bool HE, bool HEAT>
 __device__ __forceinline__ void pass_range(const StepArgs& a, const BinTables& t, const WFArgs& w, int S) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const int64_t n = (int64_t)__ldcg(w.count_in);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // the previous pass used the next pass's counter and has finished
+  if (blockIdx.x == 0 && threadIdx.x == 0) *w.work_next = 0u;
   Tally tl{0, 0, 0, 0u, 0u};
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+  for (;;) {
+    const int64_t base = next_block_packets(w.work);
+    if (base >= n) break;
     const int64_t j = base + threadIdx.x;
     int b = -1;
     bool alive = false;
@@ -924,9 +941,10 @@ __device__ __forceinline__ void pass_range_q(const StepArgs& a, const BinTables&
                                              bool read_sorted, bool write_keys, int curve) {
   const int nb = NBT > 0 ? NBT : t.n_bins;
   const int64_t n = (int64_t)__ldcg(wf.count + CUR);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   Tally tl{0, 0, 0, 0u, 0u};
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+  for (;;) {
+    const int64_t base = next_block_packets(wf.count + 2);   // cleared before the pass
+    if (base >= n) break;
     const int64_t j = base + threadIdx.x;
     int b = -1;
     bool alive = false;
@@ -1180,6 +1198,8 @@ __host__ __device__ __forceinline__ WFArgs wf_args(const WF& wf, int in, bool re
   w.bcount = wf.bcount;
   w.rs = wf.rs;
   w.cap = wf.cap;
+  w.work = nullptr;
+  w.work_next = nullptr;
   return w;
 }
 WFArgs wf_args(WF* wf, int in, bool read_sorted, bool write_keys, int tile = 0, int curve = 0) {
@@ -1327,7 +1347,10 @@ __global__ void __launch_bounds__(256, MINB) k_wavefront(StepArgs a, BinTables t
       }
       if (keys_next)
         for (int64_t k = gtid; k < wf.n_keys; k += gstride) wf.bcount[k] = 0u;
-      if (gtid == 0) wf.count[1 - cur] = 0u;
+      if (gtid == 0) {
+        wf.count[1 - cur] = 0u;
+        wf.count[2] = 0u;          // the pass's work counter
+      }
       if (!grid_sync(wf.gsync, a.err)) return;
       if (cur == 0) pass_range_q<NBT, HE, HEAT, 0>(a, t, wf, S, sorted_now, keys_next, curve);
       else pass_range_q<NBT, HE, HEAT, 1>(a, t, wf, S, sorted_now, keys_next, curve);
@@ -1495,6 +1518,10 @@ int run_mixed(const StepArgs& a, const BinTables& t, const crash_run_opts& o, WF
       const bool next_sorted = sorted_pass(p + 1);
       if (next_sorted) cudaMemsetAsync(wf->bcount, 0, sizeof(unsigned) * wf->n_keys, s);
       WFArgs w = wf_args(wf, cur, sorted_pass(p), next_sorted, 0, o.sort_curve);
+      // pass p hands out its queue from count[2 + p % 2] and clears the
+      // other one for pass p + 1 (both are cleared with the chunk)
+      w.work = wf->count + 2 + (p & 1);
+      w.work_next = wf->count + 2 + ((p + 1) & 1);
       cudaMemsetAsync(w.count_out, 0, sizeof(unsigned), s);
       tic();
       if (p == 0) {
