@@ -296,7 +296,8 @@ def run_crash(args):
     g = native.Grid(boxes, prec)
     graph = bool(args.graph)
     pers = {"persistent": 1, "per-pass": 0}.get(args.launch, 1)
-    g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0, persistent=pers)
+    g.set_options(timing=0 if graph else 1, use_graph=1 if graph else 0, persistent=pers,
+                  reg_cap=args.reg_cap)
     stream = torch.cuda.ExternalStream(g.stream(), device=dev)
     state_bytes = ncell_all * (4 + 4 * 8 + 32 + (32 if prec == native.CRASH_FP64_PLAIN else 16))
     l2_bytes = 129 * 2**20
@@ -580,6 +581,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--packets", type=int, default=0, help="override packets per step (small cases)")
+    ap.add_argument("--reg-cap", type=int, default=0, choices=[0, 1],
+                    help="without autotuning: 1 = transport kernels capped at 64 registers")
     ap.add_argument("--one-by-one", action="store_true",
                     help="batched workloads: also time the same boxes stepped one at a time")
     ap.add_argument("--launch", default="auto", choices=["auto", "persistent", "per-pass"],
